@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: long CPU test (full-size workloads)")
+
+
+@pytest.fixture(scope="session")
+def tiny_forest():
+    import datagen
+    return datagen.forest("tiny")
+
+
+@pytest.fixture(scope="session")
+def tiny_rows():
+    import datagen
+    return datagen.test_rows("tiny")
