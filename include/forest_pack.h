@@ -1,0 +1,205 @@
+/*
+ * forest_pack.h -- C ABI of the GB300 forest-packing classification library.
+ *
+ * The library classifies batches of observations with a trained decision
+ * forest stored in the packed layout of "Forest Packing: Fast, Parallel
+ * Decision Forests" (Browne et al.):
+ *   - trees are grouped into bins of B trees (Section III, "T/B bins");
+ *   - levels 0..d of a bin's trees are interleaved into one contiguous block
+ *     (Section III-A, Bin layout; d = 0 interleaves the roots only, Fig. 2);
+ *   - deeper nodes are laid out per tree depth-first with the child of larger
+ *     training cardinality adjacent to its parent (Section III-A, Stat);
+ *   - leaves are not stored as nodes: their class is folded into the parent
+ *     (Section III-A, DF-, which replaces leaves with per-class nodes);
+ * and reduces the per-tree leaf classes to a majority vote.
+ *
+ * Conventions for every entry point:
+ *   - Return FP_OK (0) or a negative FP_E* code; no C++ exception crosses the
+ *     boundary.  fp_last_error() returns a thread-local message for the last
+ *     failing call on the calling thread.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on it; an argument
+ *     error is reported before anything is enqueued.  Errors raised inside a
+ *     kernel (a bounded wait that ran out, a corrupt record) are recorded in
+ *     the forest's device status word and reported by fp_sync_status().
+ *   - Pointers marked "device" must be device (or managed) memory of the
+ *     current device; "host" pointers are ordinary host memory.  The caller
+ *     owns every buffer it passes; the library owns every object it returns
+ *     through an out-pointer until the matching release call.
+ *   - n == 0 is valid and enqueues nothing.  A NULL optional output is skipped.
+ *   - Split rule: x[feature] <= threshold goes to the left child, otherwise
+ *     (including NaN) to the right child, compared in IEEE FP32 without
+ *     flushing subnormals.  Vote ties go to the lowest class index.  (The paper
+ *     states neither rule.)
+ */
+#ifndef FOREST_PACK_H
+#define FOREST_PACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FP_OK 0
+#define FP_EINVAL (-1)       /* bad argument or malformed forest */
+#define FP_ENOMEM (-2)       /* host or device allocation failed */
+#define FP_ECUDA (-3)        /* a CUDA runtime call failed */
+#define FP_EUNSUPPORTED (-4) /* forest exceeds a field width of the record format */
+#define FP_ETIMEOUT (-5)     /* a bounded device wait ran out */
+#define FP_EDEVICE (-6)      /* a kernel reported a corrupt record or index */
+
+/* A trained forest (Section III: T binary trees, each internal node a split
+ * condition with two children, each leaf one class label).  Host memory,
+ * owned by the caller, read only during fp_pack_forest / fp_plain_build.
+ * Node arrays are concatenated per tree; node ids are tree-local and node 0
+ * of each tree is its root. */
+typedef struct fp_forest_desc {
+    int32_t n_trees;                /* T >= 1 */
+    int32_t n_features;             /* 1 .. 1024 */
+    int32_t n_classes;              /* 1 .. 512 */
+    const int64_t *tree_node_begin; /* [T+1] offsets into the node arrays */
+    const int32_t *left;            /* child id, tree-local; -1 marks a leaf */
+    const int32_t *right;           /* child id, tree-local; -1 on leaves */
+    const int32_t *feature;         /* split feature (internal nodes) */
+    const float *threshold;         /* split threshold (internal nodes) */
+    const int32_t *leaf_class;      /* class label (leaves) */
+    const int64_t *cardinality;     /* training count reaching the node; used to
+                                       order children (Section III-A, Stat).
+                                       NULL: children keep left-first order. */
+} fp_forest_desc;
+
+/* Layout and launch parameters; 0 selects the default (for interleave_depth,
+ * -1 does, since 0 is a valid depth).
+ *   bin_size          B, trees per bin (Section III-A "stripe width"), 1..1024
+ *   interleave_depth  d, levels 0..d interleaved per bin (Section III-A), 0..9
+ *   obs_tile          observations per work item of the traversal kernel,
+ *                     a multiple of 32, up to 2048
+ *   warps_per_cta     warps per CTA of the traversal kernel, 1..32
+ *   pass_bytes        bins are swept in groups ("passes") whose records fit in
+ *                     this many bytes, so a pass stays resident in L2 while
+ *                     every observation tile walks it; 0 = default (48 MiB),
+ *                     negative = one pass over the whole forest */
+typedef struct fp_pack_params {
+    int32_t bin_size;
+    int32_t interleave_depth;
+    int32_t obs_tile;
+    int32_t warps_per_cta;
+    int64_t pass_bytes;
+} fp_pack_params;
+
+typedef struct fp_packed_forest fp_packed_forest; /* host image, opaque */
+typedef struct fp_device_forest fp_device_forest; /* resident on one device, opaque */
+
+/* Sizes of a packed image (for tests, memory planning and the roofline). */
+typedef struct fp_packed_info {
+    int32_t n_trees, n_features, n_classes;
+    int32_t bin_size, interleave_depth, n_bins;
+    int32_t obs_tile, warps_per_cta;
+    int64_t n_deep_records;   /* 8-byte records below the interleaved levels */
+    int64_t head_bytes;       /* all bins' interleaved blocks (+ link rows) */
+    int64_t deep_bytes;       /* n_deep_records * 8 */
+    int64_t total_bytes;      /* bytes uploaded for classification */
+    int64_t parity_bytes;     /* leaf-id side tables, uploaded for fp_predict_leaves */
+    int32_t max_head_bytes;   /* largest single bin block (staged in shared memory) */
+    int32_t passes;           /* bin groups swept one after another (L2 blocking) */
+} fp_packed_info;
+
+/* Build the packed host image of a forest (Section III-A: DF-, Stat, Bin).
+ * desc: host, caller-owned.  params: may be NULL (all defaults).
+ * *out: library-owned until fp_release_packed.
+ * Errors: FP_EINVAL (malformed forest: bad child ids, cycles, classes or
+ * features out of range), FP_EUNSUPPORTED (a tree below the interleaved levels
+ * holds 2^19 records or more), FP_ENOMEM. */
+int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *params, fp_packed_forest **out);
+
+/* Fill *info with the sizes of a packed image.  Host only. */
+int fp_packed_info_get(const fp_packed_forest *pf, fp_packed_info *info);
+
+/* The packed host image itself, for host-side decoding tests: the bytes that
+ * fp_upload copies (*bytes receives the size).  Library-owned; valid until
+ * fp_release_packed.  Returns NULL on bad arguments. */
+const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes);
+
+/* Copy a packed image to the current device on `stream` and return a
+ * resident forest (library-owned until fp_release).  The host image may be
+ * released once the call returns (the copy is staged through library-owned
+ * pinned memory).  Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA. */
+int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_forest **out);
+
+/* Classify n observations (Section III; Section III-B evaluates a bin's
+ * trees together, here a CTA walks a bin's trees for a tile of observations).
+ *   X          device, [n][n_features] FP32 row-major, contiguous rows
+ *   out_votes  device, [n][n_classes] uint32 per-class leaf counts, or NULL
+ *   out_class  device, [n] int32 argmax of the votes (lowest class on ties),
+ *              or NULL
+ * Asynchronous on `stream`; X must stay valid and the outputs untouched until
+ * the stream reaches this work.  Calls on different streams may overlap.
+ * Errors: FP_EINVAL, FP_ENOMEM (stream-ordered scratch), FP_ECUDA. */
+int fp_predict(const fp_device_forest *forest, const float *X, int64_t n, uint32_t *out_votes, int32_t *out_class,
+               void *stream);
+
+/* Parity mode: the leaf each observation reaches in each tree.
+ *   out_leaf   device, [n][n_trees] int32, tree-local node id of the leaf in
+ *              the fp_forest_desc the forest was packed from
+ * Errors as fp_predict. */
+int fp_predict_leaves(const fp_device_forest *forest, const float *X, int64_t n, int32_t *out_leaf, void *stream);
+
+/* One launch over several resident forests and uneven batches (the batching
+ * pattern: many forests and observation batches in one persistent kernel,
+ * suitable for CUDA-graph capture).  Every element is as in fp_predict. */
+typedef struct fp_batch {
+    const float *X;      /* device [n][n_features of its forest] */
+    int64_t n;
+    uint32_t *out_votes; /* device [n][n_classes] or NULL */
+    int32_t *out_class;  /* device [n] or NULL */
+} fp_batch;
+int fp_predict_batched(const fp_device_forest *const *forests, const fp_batch *batches, int32_t k, void *stream);
+
+/* Wait for `stream` and report the forest's device status word: FP_OK, or the
+ * first error a kernel recorded since the last call (FP_ETIMEOUT,
+ * FP_EDEVICE).  Clears the word.  Blocks the calling host thread. */
+int fp_sync_status(const fp_device_forest *forest, void *stream);
+
+/* Sizes of a resident forest (same fields as fp_packed_info_get). */
+int fp_device_info_get(const fp_device_forest *forest, fp_packed_info *info);
+
+void fp_release_packed(fp_packed_forest *pf); /* NULL is a no-op */
+void fp_release(fp_device_forest *forest);     /* NULL is a no-op; synchronises the device */
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char *fp_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Plain baseline: the breadth-first per-tree layout the paper measures its
+ * layouts against (Section III-A, BF; Section IV-B uses BF as the baseline),
+ * evaluated the plain GPU way: one thread per (observation, tree), global
+ * atomic votes, then a separate argmax kernel.
+ * ------------------------------------------------------------------------ */
+typedef struct fp_plain_forest fp_plain_forest;
+
+#define FP_PLAIN_OBS_FASTEST 0  /* consecutive threads: same tree, next observation */
+#define FP_PLAIN_TREE_FASTEST 1 /* consecutive threads: same observation, next tree */
+
+/* Build the BF layout of desc and copy it to the current device on stream.
+ * *out library-owned until fp_plain_release.  Errors: FP_EINVAL, FP_ENOMEM,
+ * FP_ECUDA. */
+int fp_plain_build(const fp_forest_desc *desc, void *stream, fp_plain_forest **out);
+
+/* Classify with the plain layout.  out_votes (device [n][C] uint32) is
+ * required: it is zeroed on the stream and accumulated with atomics;
+ * out_class (device [n] int32) may be NULL.  order: FP_PLAIN_*. */
+int fp_plain_predict(const fp_plain_forest *pf, const float *X, int64_t n, int32_t order, uint32_t *out_votes,
+                     int32_t *out_class, void *stream);
+
+/* Bytes of the plain layout on the device. */
+int64_t fp_plain_bytes(const fp_plain_forest *pf);
+
+void fp_plain_release(fp_plain_forest *pf); /* NULL is a no-op */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOREST_PACK_H */

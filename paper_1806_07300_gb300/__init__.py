@@ -1,0 +1,356 @@
+"""Python binding of the forest-packing C ABI (include/forest_pack.h).
+
+Argument marshalling only: every step of classification runs in the CUDA
+library ``libforestpack.so`` built in-tree for sm_103a.  There is no CPU
+fallback; importing the binding fails loudly when the library is missing.
+PyTorch supplies device memory and streams.
+
+Names follow the C ABI: :func:`fp_pack_forest`, :func:`fp_upload`,
+:func:`fp_predict`, :func:`fp_predict_leaves`, :func:`fp_predict_batched`,
+:func:`fp_sync_status`, :func:`fp_release`, the plain baseline
+:func:`fp_plain_build` / :func:`fp_plain_predict`, plus small wrapper classes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+FP_OK, FP_EINVAL, FP_ENOMEM, FP_ECUDA, FP_EUNSUPPORTED, FP_ETIMEOUT, FP_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+FP_PLAIN_OBS_FASTEST, FP_PLAIN_TREE_FASTEST = 0, 1
+_ERRNAMES = {-1: "FP_EINVAL", -2: "FP_ENOMEM", -3: "FP_ECUDA", -4: "FP_EUNSUPPORTED", -5: "FP_ETIMEOUT",
+             -6: "FP_EDEVICE"}
+
+
+class FPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fp_forest_desc(ctypes.Structure):
+    _fields_ = [("n_trees", ctypes.c_int32), ("n_features", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("tree_node_begin", ctypes.c_void_p), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
+                ("feature", ctypes.c_void_p), ("threshold", ctypes.c_void_p), ("leaf_class", ctypes.c_void_p),
+                ("cardinality", ctypes.c_void_p)]
+
+
+class fp_pack_params(ctypes.Structure):
+    _fields_ = [("bin_size", ctypes.c_int32), ("interleave_depth", ctypes.c_int32), ("obs_tile", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("pass_bytes", ctypes.c_int64)]
+
+
+class fp_packed_info(ctypes.Structure):
+    _fields_ = [("n_trees", ctypes.c_int32), ("n_features", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("bin_size", ctypes.c_int32), ("interleave_depth", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("obs_tile", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("n_deep_records", ctypes.c_int64), ("head_bytes", ctypes.c_int64), ("deep_bytes", ctypes.c_int64),
+                ("total_bytes", ctypes.c_int64), ("parity_bytes", ctypes.c_int64),
+                ("max_head_bytes", ctypes.c_int32), ("passes", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fp_batch(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("out_votes", ctypes.c_void_p),
+                ("out_class", ctypes.c_void_p)]
+
+
+# every symbol include/forest_pack.h declares
+EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
+           "fp_predict_leaves", "fp_predict_batched", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
+           "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
+           "fp_plain_release"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libforestpack.so (building it first if its sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"CUDA library {LIB_PATH} is missing; run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            sig = {
+                "fp_pack_forest": ([ctypes.POINTER(fp_forest_desc), ctypes.POINTER(fp_pack_params),
+                                    ctypes.POINTER(P)], ctypes.c_int),
+                "fp_packed_info_get": ([P, ctypes.POINTER(fp_packed_info)], ctypes.c_int),
+                "fp_packed_image": ([P, ctypes.POINTER(i64)], P),
+                "fp_upload": ([P, P, ctypes.POINTER(P)], ctypes.c_int),
+                "fp_predict": ([P, P, i64, P, P, P], ctypes.c_int),
+                "fp_predict_leaves": ([P, P, i64, P, P], ctypes.c_int),
+                "fp_predict_batched": ([P, P, i32, P], ctypes.c_int),
+                "fp_sync_status": ([P, P], ctypes.c_int),
+                "fp_device_info_get": ([P, ctypes.POINTER(fp_packed_info)], ctypes.c_int),
+                "fp_release_packed": ([P], None),
+                "fp_release": ([P], None),
+                "fp_last_error": ([], ctypes.c_char_p),
+                "fp_plain_build": ([ctypes.POINTER(fp_forest_desc), P, ctypes.POINTER(P)], ctypes.c_int),
+                "fp_plain_predict": ([P, P, i64, i32, P, P, P], ctypes.c_int),
+                "fp_plain_bytes": ([P], i64),
+                "fp_plain_release": ([P], None),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def fp_last_error() -> str:
+    return lib().fp_last_error().decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != FP_OK:
+        raise FPError(rc, f"{what}: {fp_last_error()}")
+
+
+# ----------------------------------------------------------------- helpers
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def make_desc(forest, keep: list) -> fp_forest_desc:
+    """fp_forest_desc over a forest object with the datagen.Forest fields.
+    ``keep`` collects the arrays that must outlive the descriptor."""
+    arrs = [_np(forest.node_begin, np.int64), _np(forest.left, np.int32), _np(forest.right, np.int32),
+            _np(forest.feature, np.int32), _np(forest.threshold, np.float32), _np(forest.leaf_class, np.int32)]
+    card = getattr(forest, "cardinality", None)
+    arrs.append(_np(card, np.int64) if card is not None else None)
+    keep.extend(a for a in arrs if a is not None)
+    d = fp_forest_desc()
+    d.n_trees = int(forest.n_trees)
+    d.n_features = int(forest.n_features)
+    d.n_classes = int(forest.n_classes)
+    (d.tree_node_begin, d.left, d.right, d.feature, d.threshold, d.leaf_class) = [a.ctypes.data for a in arrs[:6]]
+    d.cardinality = arrs[6].ctypes.data if arrs[6] is not None else None
+    return d
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype, shape=None, name="tensor"):
+    """Device pointer of a CUDA tensor after checking dtype, contiguity and shape."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------ C-ABI mirrors
+
+def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_tile: int = 0,
+                   warps_per_cta: int = 0, pass_bytes: int = 0) -> "PackedForest":
+    keep: list = []
+    desc = make_desc(forest, keep)
+    params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes)
+    out = ctypes.c_void_p()
+    _check(lib().fp_pack_forest(ctypes.byref(desc), ctypes.byref(params), ctypes.byref(out)), "fp_pack_forest")
+    return PackedForest(out.value, forest)
+
+
+def fp_upload(packed: "PackedForest", stream=None) -> "DeviceForest":
+    out = ctypes.c_void_p()
+    _check(lib().fp_upload(packed.handle, _stream_ptr(stream), ctypes.byref(out)), "fp_upload")
+    return DeviceForest(out.value, packed.info())
+
+
+def fp_predict(forest: "DeviceForest", X, out_votes=None, out_class=None, stream=None) -> None:
+    n = X.shape[0]
+    info = forest.info
+    xp = _dptr(X, _torch().float32, (n, info["n_features"]), "X")
+    vp = _dptr(out_votes, _torch().int32, (n, info["n_classes"]), "out_votes") if out_votes is not None else None
+    cp = _dptr(out_class, _torch().int32, (n,), "out_class") if out_class is not None else None
+    _check(lib().fp_predict(forest.handle, xp, n, vp, cp, _stream_ptr(stream)), "fp_predict")
+
+
+def fp_predict_leaves(forest: "DeviceForest", X, out_leaf, stream=None) -> None:
+    n = X.shape[0]
+    info = forest.info
+    xp = _dptr(X, _torch().float32, (n, info["n_features"]), "X")
+    lp = _dptr(out_leaf, _torch().int32, (n, info["n_trees"]), "out_leaf")
+    _check(lib().fp_predict_leaves(forest.handle, xp, n, lp, _stream_ptr(stream)), "fp_predict_leaves")
+
+
+def fp_predict_batched(forests, Xs, out_votes=None, out_class=None, stream=None) -> None:
+    k = len(forests)
+    arr = (fp_batch * max(k, 1))()
+    handles = (ctypes.c_void_p * max(k, 1))()
+    T = _torch()
+    for i, (f, X) in enumerate(zip(forests, Xs)):
+        n = X.shape[0]
+        arr[i].X = _dptr(X, T.float32, (n, f.info["n_features"]), "X")
+        arr[i].n = n
+        v = out_votes[i] if out_votes is not None else None
+        c = out_class[i] if out_class is not None else None
+        arr[i].out_votes = _dptr(v, T.int32, (n, f.info["n_classes"]), "out_votes") if v is not None else None
+        arr[i].out_class = _dptr(c, T.int32, (n,), "out_class") if c is not None else None
+        handles[i] = f.handle
+    _check(lib().fp_predict_batched(handles, arr, k, _stream_ptr(stream)), "fp_predict_batched")
+
+
+def fp_sync_status(forest: "DeviceForest", stream=None) -> int:
+    return lib().fp_sync_status(forest.handle, _stream_ptr(stream))
+
+
+def fp_release(forest: "DeviceForest") -> None:
+    forest.release()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class PackedForest:
+    """Host image made by fp_pack_forest (library-owned)."""
+
+    def __init__(self, handle: int, forest=None):
+        self.handle = handle
+        self.forest = forest
+
+    def info(self) -> dict:
+        i = fp_packed_info()
+        _check(lib().fp_packed_info_get(self.handle, ctypes.byref(i)), "fp_packed_info_get")
+        return i.as_dict()
+
+    def image(self) -> np.ndarray:
+        """A copy of the packed image bytes."""
+        nbytes = ctypes.c_int64()
+        p = lib().fp_packed_image(self.handle, ctypes.byref(nbytes))
+        if not p:
+            raise FPError(FP_EINVAL, fp_last_error())
+        return np.frombuffer((ctypes.c_uint8 * nbytes.value).from_address(p), dtype=np.uint8).copy()
+
+    def release(self) -> None:
+        if self.handle:
+            lib().fp_release_packed(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class DeviceForest:
+    """A packed forest resident on the current device (fp_upload)."""
+
+    def __init__(self, handle: int, info: dict):
+        self.handle = handle
+        i = fp_packed_info()
+        _check(lib().fp_device_info_get(handle, ctypes.byref(i)), "fp_device_info_get")
+        self.info = i.as_dict()
+
+    def predict(self, X, votes: bool = True, classes: bool = True, stream=None):
+        T = _torch()
+        n = X.shape[0]
+        v = T.empty((n, self.info["n_classes"]), dtype=T.int32, device=X.device) if votes else None
+        c = T.empty((n,), dtype=T.int32, device=X.device) if classes else None
+        fp_predict(self, X, v, c, stream)
+        return v, c
+
+    def predict_leaves(self, X, stream=None):
+        T = _torch()
+        out = T.empty((X.shape[0], self.info["n_trees"]), dtype=T.int32, device=X.device)
+        fp_predict_leaves(self, X, out, stream)
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return fp_sync_status(self, stream)
+
+    def release(self) -> None:
+        if self.handle:
+            lib().fp_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class PlainForest:
+    """The plain breadth-first baseline resident on the current device."""
+
+    def __init__(self, forest, stream=None):
+        keep: list = []
+        desc = make_desc(forest, keep)
+        out = ctypes.c_void_p()
+        _check(lib().fp_plain_build(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(out)), "fp_plain_build")
+        self.handle = out.value
+        self.n_trees, self.n_features, self.n_classes = forest.n_trees, forest.n_features, forest.n_classes
+
+    def nbytes(self) -> int:
+        return lib().fp_plain_bytes(self.handle)
+
+    def predict(self, X, order: int = FP_PLAIN_OBS_FASTEST, out_votes=None, out_class=None, stream=None):
+        T = _torch()
+        n = X.shape[0]
+        if out_votes is None:
+            out_votes = T.empty((n, self.n_classes), dtype=T.int32, device=X.device)
+        if out_class is None:
+            out_class = T.empty((n,), dtype=T.int32, device=X.device)
+        fp_plain_predict(self, X, order, out_votes, out_class, stream)
+        return out_votes, out_class
+
+    def release(self) -> None:
+        if self.handle:
+            lib().fp_plain_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def fp_plain_build(forest, stream=None) -> PlainForest:
+    return PlainForest(forest, stream)
+
+
+def fp_plain_predict(pf: PlainForest, X, order, out_votes, out_class=None, stream=None) -> None:
+    T = _torch()
+    n = X.shape[0]
+    xp = _dptr(X, T.float32, (n, pf.n_features), "X")
+    vp = _dptr(out_votes, T.int32, (n, pf.n_classes), "out_votes")
+    cp = _dptr(out_class, T.int32, (n,), "out_class") if out_class is not None else None
+    _check(lib().fp_plain_predict(pf.handle, xp, n, order, vp, cp, _stream_ptr(stream)), "fp_plain_predict")

@@ -1,0 +1,316 @@
+// fp_device.cu -- resident forests and the classification entry points.
+//
+// fp_upload copies a packed image to the device; fp_predict launches the
+// persistent traversal kernel (fp_traverse.cuh) on the caller's stream.  The
+// kernel needs scratch memory only when a forest is swept in several passes
+// (a vote accumulator when the caller asks for classes only, and one counter
+// per observation tile); that scratch comes from a library-owned
+// stream-ordered memory pool, so calls on different streams never share it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/forest_pack.h"
+#include "fp_common.h"
+#include "fp_internal.h"
+#include "fp_traverse.cuh"
+
+struct fp_device_forest {
+    int device = -1;
+    FpImageHeader hdr{};
+    std::vector<FpBin> bins;
+    std::vector<FpPass> passes;
+    uint8_t *d_image = nullptr;
+    int32_t *d_status = nullptr;
+    int32_t R = 0;            // observation tile actually launched (fits shared memory)
+    int32_t P = 0;            // shared-memory row stride (floats)
+    int32_t threads = 0;
+    int32_t head_smem = 0;
+    size_t smem_votes = 0, smem_leaves = 0;
+    int32_t grid_votes = 0, grid_leaves = 0;  // resident CTAs for a persistent launch
+};
+
+namespace {
+
+std::mutex g_pool_mu;
+std::vector<cudaMemPool_t> g_pools;
+
+int cuda_fail(cudaError_t e, const char *what) {
+    fp_set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ECUDA;
+}
+
+// Library-owned stream-ordered pool for per-call scratch, one per device.
+int scratch_pool(int device, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= device) g_pools.resize((size_t)device + 1, nullptr);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+        uint64_t keep = UINT64_MAX;  // keep freed scratch in the pool between calls
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
+        g_pools[device] = pool;
+    }
+    *out = g_pools[device];
+    return FP_OK;
+}
+
+size_t smem_bytes(int R, int P, int head_smem, int C, bool leaves) {
+    size_t xs = ((size_t)R * P * 4 + 15) & ~(size_t)15;
+    return xs + (size_t)head_smem + (leaves ? 0 : (size_t)R * C * 4);
+}
+
+template <bool LEAVES>
+int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
+    cudaError_t e = cudaFuncSetAttribute(fp_traverse_kernel<LEAVES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_traverse_kernel<LEAVES>, f->threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) {
+        fp_set_error("traversal kernel does not fit on an SM (%zu bytes of shared memory)", smem);
+        return FP_EUNSUPPORTED;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    *grid = per_sm * sms;
+    return FP_OK;
+}
+
+TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
+    TravParams p;
+    memset(&p, 0, sizeof p);
+    const FpImageHeader &h = f->hdr;
+    p.deep = reinterpret_cast<const uint2 *>(f->d_image + h.off_deep);
+    p.heads = f->d_image + h.off_heads;
+    p.bins = reinterpret_cast<const FpBin *>(f->d_image + h.off_bins);
+    p.passes = reinterpret_cast<const FpPass *>(f->d_image + h.off_passes);
+    p.tree_base = reinterpret_cast<const uint32_t *>(f->d_image + h.off_tree_base);
+    p.pheads = reinterpret_cast<const int32_t *>(f->d_image + h.off_pheads);
+    p.deep_leaf = reinterpret_cast<const int2 *>(f->d_image + h.off_deep_leaf);
+    p.X = X;
+    p.n = n;
+    p.F = h.n_features;
+    p.P = f->P;
+    p.C = h.n_classes;
+    p.T = h.n_trees;
+    p.S = h.slots;
+    p.Lk = h.links;
+    p.R = f->R;
+    p.n_tiles = (n + f->R - 1) / f->R;
+    p.head_smem = f->head_smem;
+    p.status = f->d_status;
+    return p;
+}
+
+int check_device(const fp_device_forest *f) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != f->device) {
+        fp_set_error("forest lives on device %d but device %d is current", f->device, dev);
+        return FP_EINVAL;
+    }
+    return FP_OK;
+}
+
+}  // namespace
+
+extern "C" int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_forest **out) {
+    if (!out || !pf) {
+        fp_set_error("fp_upload: NULL argument");
+        return FP_EINVAL;
+    }
+    *out = nullptr;
+    fp_device_forest *f = new (std::nothrow) fp_device_forest;
+    if (!f) {
+        fp_set_error("fp_upload: out of host memory");
+        return FP_ENOMEM;
+    }
+    const FpImageHeader *h = fp_packed_header(pf);
+    f->hdr = *h;
+    const uint8_t *img = fp_packed_bytes(pf);
+    f->bins.assign(reinterpret_cast<const FpBin *>(img + h->off_bins),
+                   reinterpret_cast<const FpBin *>(img + h->off_bins) + h->n_bins);
+    f->passes.assign(reinterpret_cast<const FpPass *>(img + h->off_passes),
+                     reinterpret_cast<const FpPass *>(img + h->off_passes) + h->n_passes);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = FP_OK;
+    cudaError_t e = cudaGetDevice(&f->device);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGetDevice"); goto fail; }
+    e = cudaMalloc(&f->d_image, (size_t)h->total_bytes);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(image)"); goto fail; }
+    e = cudaMalloc(&f->d_status, 256);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(status)"); goto fail; }
+    e = cudaMemsetAsync(f->d_status, 0, 256, s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); goto fail; }
+    e = cudaMemcpyAsync(f->d_image, img, (size_t)h->total_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(image)"); goto fail; }
+    e = cudaStreamSynchronize(s);  // the caller may free the host image on return
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamSynchronize"); goto fail; }
+    {
+        f->P = h->n_features | 1;
+        f->threads = 32 * h->warps_per_cta;
+        f->head_smem = (h->max_head_bytes + 15) & ~15;
+        int max_optin = 0;
+        e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaDeviceGetAttribute"); goto fail; }
+        const size_t budget = (size_t)max_optin - 64;  // static shared variables
+        int R = h->obs_tile;
+        while (R > 32 && smem_bytes(R, f->P, f->head_smem, h->n_classes, false) > budget) R -= 32;
+        if (smem_bytes(R, f->P, f->head_smem, h->n_classes, false) > budget) {
+            fp_set_error("fp_upload: a 32-row tile and one bin block need %zu bytes of shared memory (limit %zu)",
+                         smem_bytes(R, f->P, f->head_smem, h->n_classes, false), budget);
+            rc = FP_EUNSUPPORTED;
+            goto fail;
+        }
+        f->R = R;
+        f->smem_votes = smem_bytes(R, f->P, f->head_smem, h->n_classes, false);
+        f->smem_leaves = smem_bytes(R, f->P, f->head_smem, h->n_classes, true);
+        rc = configure<false>(f, f->smem_votes, &f->grid_votes);
+        if (rc) goto fail;
+        rc = configure<true>(f, f->smem_leaves, &f->grid_leaves);
+        if (rc) goto fail;
+    }
+    *out = f;
+    return FP_OK;
+fail:
+    if (f->d_image) cudaFree(f->d_image);
+    if (f->d_status) cudaFree(f->d_status);
+    delete f;
+    return rc;
+}
+
+extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, uint32_t *out_votes,
+                          int32_t *out_class, void *stream) {
+    if (!f || n < 0 || (n > 0 && !X)) {
+        fp_set_error("fp_predict: bad arguments");
+        return FP_EINVAL;
+    }
+    if (n == 0 || (!out_votes && !out_class)) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const FpImageHeader &h = f->hdr;
+    TravParams p = base_params(f, X, n);
+    p.n_passes = h.n_passes;
+    p.n_items = p.n_tiles * h.n_passes;
+    p.out_votes = out_votes;
+    p.out_class = out_class;
+    void *scratch = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e;
+    if (h.n_passes > 1) {
+        const size_t vote_bytes = out_votes ? 0 : (size_t)n * h.n_classes * 4;
+        const size_t cnt_bytes = out_class ? (size_t)p.n_tiles * 4 : 0;
+        const size_t bytes = ((vote_bytes + 255) & ~(size_t)255) + cnt_bytes;
+        if (bytes) {
+            rc = scratch_pool(f->device, &pool);
+            if (rc) return rc;
+            e = cudaMallocFromPoolAsync(&scratch, bytes, pool, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
+            e = cudaMemsetAsync(scratch, 0, bytes, s);
+            if (e != cudaSuccess) { cudaFreeAsync(scratch, s); return cuda_fail(e, "cudaMemsetAsync(scratch)"); }
+        }
+        uint8_t *sc = static_cast<uint8_t *>(scratch);
+        p.acc = out_votes ? out_votes : reinterpret_cast<uint32_t *>(sc);
+        p.tile_done = reinterpret_cast<uint32_t *>(sc + ((vote_bytes + 255) & ~(size_t)255));
+        if (out_votes) {
+            e = cudaMemsetAsync(out_votes, 0, (size_t)n * h.n_classes * 4, s);
+            if (e != cudaSuccess) {
+                if (scratch) cudaFreeAsync(scratch, s);
+                return cuda_fail(e, "cudaMemsetAsync(out_votes)");
+            }
+        }
+    }
+    const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
+    fp_traverse_kernel<false><<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    e = cudaGetLastError();
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
+    return FP_OK;
+}
+
+extern "C" int fp_predict_leaves(const fp_device_forest *f, const float *X, int64_t n, int32_t *out_leaf,
+                                 void *stream) {
+    if (!f || n < 0 || (n > 0 && (!X || !out_leaf))) {
+        fp_set_error("fp_predict_leaves: bad arguments");
+        return FP_EINVAL;
+    }
+    if (n == 0) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    TravParams p = base_params(f, X, n);
+    p.n_passes = f->hdr.n_passes;
+    p.n_items = p.n_tiles * f->hdr.n_passes;
+    p.out_leaf = out_leaf;
+    const int64_t grid = std::min<int64_t>(p.n_items, f->grid_leaves);
+    fp_traverse_kernel<true><<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<leaves> launch");
+    return FP_OK;
+}
+
+extern "C" int fp_sync_status(const fp_device_forest *f, void *stream) {
+    if (!f) {
+        fp_set_error("fp_sync_status: NULL forest");
+        return FP_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int32_t word = 0;
+    e = cudaMemcpy(&word, f->d_status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    if (word != 0) {
+        e = cudaMemset(f->d_status, 0, 4);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        fp_set_error("a kernel reported status %d", word);
+        return word < 0 ? word : FP_EDEVICE;
+    }
+    return FP_OK;
+}
+
+extern "C" int fp_device_info_get(const fp_device_forest *f, fp_packed_info *info) {
+    if (!f || !info) {
+        fp_set_error("fp_device_info_get: NULL argument");
+        return FP_EINVAL;
+    }
+    fp_fill_info(&f->hdr, info);
+    info->obs_tile = f->R;
+    return FP_OK;
+}
+
+extern "C" void fp_release(fp_device_forest *f) {
+    if (!f) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != f->device) cudaSetDevice(f->device);
+    cudaDeviceSynchronize();
+    cudaFree(f->d_image);
+    cudaFree(f->d_status);
+    if (prev >= 0 && prev != f->device) cudaSetDevice(prev);
+    delete f;
+}
+
+// Internal accessors for the batched entry point.
+const FpImageHeader *fp_dev_header(const fp_device_forest *f) { return &f->hdr; }
+TravParams fp_dev_params(const fp_device_forest *f, const float *X, int64_t n) { return base_params(f, X, n); }
+int fp_dev_device(const fp_device_forest *f) { return f->device; }
+int fp_dev_threads(const fp_device_forest *f) { return f->threads; }
+size_t fp_dev_smem(const fp_device_forest *f) { return f->smem_votes; }

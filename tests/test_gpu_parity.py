@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element.
+
+Everything on this path is integer control flow plus FP32 compares, so the
+bar is bit-exactness: per-tree leaf ids, vote counts and classes must equal
+the oracle's on the same seeded inputs (tolerance 0)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_1806_07300_gb300 as fp
+from golden_io import load
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda()
+
+
+def _check_all(forest, X, ref=None, **params):
+    if ref is None:
+        ref = oracle.predict(forest, X, threads=oracle.default_threads())
+    pk = fp.fp_pack_forest(forest, **params)
+    df = fp.fp_upload(pk)
+    Xd = _dev(X)
+    votes, cls = df.predict(Xd)
+    leaves = df.predict_leaves(Xd)
+    torch.cuda.synchronize()
+    assert df.sync_status() == fp.FP_OK
+    np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
+    np.testing.assert_array_equal(votes.cpu().numpy().astype(np.uint32), ref["votes"])
+    np.testing.assert_array_equal(cls.cpu().numpy(), ref["cls"])
+    # classes only (no votes buffer) and votes only
+    _, c2 = df.predict(Xd, votes=False)
+    v3, _ = df.predict(Xd, classes=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(c2.cpu().numpy(), ref["cls"])
+    np.testing.assert_array_equal(v3.cpu().numpy().astype(np.uint32), ref["votes"])
+    df.release()
+    return ref
+
+
+@pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
+@pytest.mark.parametrize("B,d", [(1, 0), (2, 1), (3, 3)])
+def test_hand_fixtures_on_gpu(name, B, d):
+    """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs."""
+    forest, X, exp = load(name)
+    ref = dict(leaf=exp["leaf"], votes=exp["votes"], cls=exp["cls"])
+    _check_all(forest, X, ref, bin_size=B, interleave_depth=d)
+
+
+@pytest.mark.parametrize("B,d", [(16, 4), (1, 0), (5, 2), (7, 6), (16, 9)])
+def test_tiny_workload(tiny_forest, tiny_rows, B, d):
+    X, _ = tiny_rows
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d)
+
+
+@pytest.mark.parametrize("tile,warps", [(32, 1), (64, 3), (256, 8), (1024, 32)])
+def test_tiny_tiles_and_ragged_tail(tiny_forest, tiny_rows, tile, warps):
+    X, _ = tiny_rows
+    _check_all(tiny_forest, X[:tile * 3 + 17], bin_size=4, interleave_depth=2, obs_tile=tile, warps_per_cta=warps)
+
+
+@pytest.mark.parametrize("pass_bytes", [1, 4096, 65536])
+def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes):
+    """Several passes: global accumulation and last-pass argmax."""
+    X, _ = tiny_rows
+    pk = fp.fp_pack_forest(tiny_forest, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes)
+    assert pk.info()["passes"] > 1
+    _check_all(tiny_forest, X, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes, obs_tile=128)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 33])
+def test_small_and_empty_batches(tiny_forest, tiny_rows, n):
+    X, _ = tiny_rows
+    if n == 0:
+        df = fp.fp_upload(fp.fp_pack_forest(tiny_forest))
+        Xd = torch.empty((0, tiny_forest.n_features), dtype=torch.float32, device="cuda")
+        v, c = df.predict(Xd)
+        assert v.shape == (0, tiny_forest.n_classes) and c.shape == (0,)
+        df.release()
+        return
+    _check_all(tiny_forest, X[:n])
+
+
+def test_no_cardinality_keeps_left_first(tiny_forest, tiny_rows):
+    X, _ = tiny_rows
+    f = datagen.Forest(tiny_forest.n_features, tiny_forest.n_classes, tiny_forest.node_begin, tiny_forest.left,
+                       tiny_forest.right, tiny_forest.feature, tiny_forest.threshold, tiny_forest.leaf_class,
+                       tiny_forest.cardinality)
+    f.cardinality = None
+    ref = oracle.predict(tiny_forest, X)
+    _check_all(f, X, ref)
+
+
+@pytest.mark.parametrize("order", [fp.FP_PLAIN_OBS_FASTEST, fp.FP_PLAIN_TREE_FASTEST])
+def test_plain_baseline(tiny_forest, tiny_rows, order):
+    X, _ = tiny_rows
+    ref = oracle.predict(tiny_forest, X)
+    pf = fp.fp_plain_build(tiny_forest)
+    v, c = pf.predict(_dev(X), order=order)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(v.cpu().numpy().astype(np.uint32), ref["votes"])
+    np.testing.assert_array_equal(c.cpu().numpy(), ref["cls"])
+    pf.release()
+
+
+@pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
+def test_plain_baseline_fixture(name):
+    forest, X, exp = load(name)
+    pf = fp.fp_plain_build(forest)
+    v, c = pf.predict(_dev(X))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(v.cpu().numpy().astype(np.uint32), exp["votes"])
+    np.testing.assert_array_equal(c.cpu().numpy(), exp["cls"])
+
+
+def test_batched_matches_single(tiny_forest, tiny_rows):
+    X, _ = tiny_rows
+    forests, Xs, refs = [], [], []
+    for i, n in enumerate([1, 700, 33, 5000]):
+        forests.append(fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=1 + 3 * i, interleave_depth=i)))
+        Xs.append(_dev(X[i * 10: i * 10 + n]))
+        refs.append(oracle.predict(tiny_forest, X[i * 10: i * 10 + n]))
+    votes = [torch.empty((x.shape[0], tiny_forest.n_classes), dtype=torch.int32, device="cuda") for x in Xs]
+    cls = [torch.empty((x.shape[0],), dtype=torch.int32, device="cuda") for x in Xs]
+    fp.fp_predict_batched(forests, Xs, votes, cls)
+    torch.cuda.synchronize()
+    for v, c, r in zip(votes, cls, refs):
+        np.testing.assert_array_equal(v.cpu().numpy().astype(np.uint32), r["votes"])
+        np.testing.assert_array_equal(c.cpu().numpy(), r["cls"])
+
+
+def test_image_workload_10k():
+    """Image-shaped workload (784 features, 10 classes, 128 trees), 10,000 rows."""
+    forest = datagen.forest("image")
+    X, _ = datagen.test_rows("image", 10000)
+    _check_all(forest, X)
+
+
+def test_image_workload_params_grid():
+    forest = datagen.forest("image")
+    X, _ = datagen.test_rows("image", 3000)
+    ref = oracle.predict(forest, X, threads=oracle.default_threads())
+    for B, d in [(128, 1), (16, 3), (32, 6)]:
+        _check_all(forest, X, ref, bin_size=B, interleave_depth=d)
