@@ -5,12 +5,16 @@
  * forest stored in the packed layout of "Forest Packing: Fast, Parallel
  * Decision Forests" (Browne et al.):
  *   - trees are grouped into bins of B trees (Section III, "T/B bins");
- *   - levels 0..d of a bin's trees are interleaved into one contiguous block
- *     (Section III-A, Bin layout; d = 0 interleaves the roots only, Fig. 2);
- *   - deeper nodes are laid out per tree depth-first with the child of larger
- *     training cardinality adjacent to its parent (Section III-A, Stat);
- *   - leaves are not stored as nodes: their class is folded into the parent
- *     (Section III-A, DF-, which replaces leaves with per-class nodes);
+ *   - the top of each tree -- its 2^(d+1)-1 most frequently visited nodes,
+ *     levels 0..d for a complete tree -- is interleaved with the other trees
+ *     of its bin into one contiguous block (Section III-A, Bin layout; d = 0
+ *     interleaves the roots only, Fig. 2), staged into shared memory;
+ *   - deeper nodes are laid out per tree depth-first with the more frequently
+ *     reached child placed next to its parent (Section III-A, Stat), in
+ *     super-nodes of two levels that fill one 32-byte memory sector;
+ *   - leaves are not stored as nodes: their class is folded into the reference
+ *     that leads to them (Section III-A, DF-, which replaces leaves with
+ *     per-class nodes);
  * and reduces the per-tree leaf classes to a majority vote.
  *
  * Conventions for every entry point:
@@ -73,20 +77,29 @@ typedef struct fp_forest_desc {
 /* Layout and launch parameters; 0 selects the default (for interleave_depth,
  * -1 does, since 0 is a valid depth).
  *   bin_size          B, trees per bin (Section III-A "stripe width"), 1..1024
- *   interleave_depth  d, levels 0..d interleaved per bin (Section III-A), 0..9
+ *   interleave_depth  d: each tree contributes 2^(d+1)-1 nodes (levels 0..d of
+ *                     a complete tree) to its bin's interleaved block
+ *                     (Section III-A), 0..9
  *   obs_tile          observations per work item of the traversal kernel,
  *                     a multiple of 32, up to 2048
  *   warps_per_cta     warps per CTA of the traversal kernel, 1..32
  *   pass_bytes        bins are swept in groups ("passes") whose records fit in
  *                     this many bytes, so a pass stays resident in L2 while
  *                     every observation tile walks it; 0 = default (48 MiB),
- *                     negative = one pass over the whole forest */
+ *                     negative = one pass over the whole forest
+ *   refill_lanes      a warp hands new (observation, tree) tasks to its idle
+ *                     lanes once this many lanes are idle, 1..32
+ *   head_select       which 2^(d+1)-1 nodes of a tree form its interleaved head:
+ *                     0 = those of highest training cardinality (the popular
+ *                     paths of Section III-A), 1 = levels 0..d exactly */
 typedef struct fp_pack_params {
     int32_t bin_size;
     int32_t interleave_depth;
     int32_t obs_tile;
     int32_t warps_per_cta;
     int64_t pass_bytes;
+    int32_t refill_lanes;
+    int32_t head_select;
 } fp_pack_params;
 
 typedef struct fp_packed_forest fp_packed_forest; /* host image, opaque */
@@ -97,21 +110,27 @@ typedef struct fp_packed_info {
     int32_t n_trees, n_features, n_classes;
     int32_t bin_size, interleave_depth, n_bins;
     int32_t obs_tile, warps_per_cta;
-    int64_t n_deep_records;   /* 8-byte records below the interleaved levels */
+    int64_t n_internal;       /* internal nodes of the forest */
+    int64_t n_super;          /* 32-byte super-nodes below the interleaved levels */
     int64_t head_bytes;       /* all bins' interleaved blocks (+ link rows) */
-    int64_t deep_bytes;       /* n_deep_records * 8 */
+    int64_t deep_bytes;       /* n_super * 32 */
     int64_t total_bytes;      /* bytes uploaded for classification */
     int64_t parity_bytes;     /* leaf-id side tables, uploaded for fp_predict_leaves */
     int32_t max_head_bytes;   /* largest single bin block (staged in shared memory) */
     int32_t passes;           /* bin groups swept one after another (L2 blocking) */
+    int32_t refill_lanes;
+    int32_t head_nodes;       /* 2^(d+1)-1: head nodes per tree at most */
+    int32_t head_select;
+    int32_t reserved;
 } fp_packed_info;
 
 /* Build the packed host image of a forest (Section III-A: DF-, Stat, Bin).
  * desc: host, caller-owned.  params: may be NULL (all defaults).
  * *out: library-owned until fp_release_packed.
  * Errors: FP_EINVAL (malformed forest: bad child ids, cycles, classes or
- * features out of range), FP_EUNSUPPORTED (a tree below the interleaved levels
- * holds 2^19 records or more), FP_ENOMEM. */
+ * features out of range, bad params), FP_EUNSUPPORTED (more than 1024
+ * features or 512 classes, a bin block over 100 KiB, 2^32 super-nodes or
+ * more), FP_ENOMEM. */
 int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *params, fp_packed_forest **out);
 
 /* Fill *info with the sizes of a packed image.  Host only. */
@@ -127,6 +146,14 @@ const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes);
  * released once the call returns (the copy is staged through library-owned
  * pinned memory).  Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA. */
 int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_forest **out);
+
+/* Change the launch parameters of a resident forest: obs_tile,
+ * warps_per_cta and refill_lanes of *params (0 keeps the current value); the
+ * layout fields (bin_size, interleave_depth, pass_bytes) must be 0 or equal
+ * to the forest's.  The observation tile is lowered, if needed, to fit shared
+ * memory.  Host only; do not call while a launch on this forest is being
+ * enqueued from another thread.  Errors: FP_EINVAL, FP_EUNSUPPORTED, FP_ECUDA. */
+int fp_configure(fp_device_forest *forest, const fp_pack_params *params);
 
 /* Classify n observations (Section III; Section III-B evaluates a bin's
  * trees together, here a CTA walks a bin's trees for a tile of observations).

@@ -43,16 +43,19 @@ class fp_forest_desc(ctypes.Structure):
 
 class fp_pack_params(ctypes.Structure):
     _fields_ = [("bin_size", ctypes.c_int32), ("interleave_depth", ctypes.c_int32), ("obs_tile", ctypes.c_int32),
-                ("warps_per_cta", ctypes.c_int32), ("pass_bytes", ctypes.c_int64)]
+                ("warps_per_cta", ctypes.c_int32), ("pass_bytes", ctypes.c_int64), ("refill_lanes", ctypes.c_int32),
+                ("head_select", ctypes.c_int32)]
 
 
 class fp_packed_info(ctypes.Structure):
     _fields_ = [("n_trees", ctypes.c_int32), ("n_features", ctypes.c_int32), ("n_classes", ctypes.c_int32),
                 ("bin_size", ctypes.c_int32), ("interleave_depth", ctypes.c_int32), ("n_bins", ctypes.c_int32),
                 ("obs_tile", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("n_deep_records", ctypes.c_int64), ("head_bytes", ctypes.c_int64), ("deep_bytes", ctypes.c_int64),
+                ("n_internal", ctypes.c_int64), ("n_super", ctypes.c_int64), ("head_bytes", ctypes.c_int64),
+                ("deep_bytes", ctypes.c_int64),
                 ("total_bytes", ctypes.c_int64), ("parity_bytes", ctypes.c_int64),
-                ("max_head_bytes", ctypes.c_int32), ("passes", ctypes.c_int32)]
+                ("max_head_bytes", ctypes.c_int32), ("passes", ctypes.c_int32), ("refill_lanes", ctypes.c_int32),
+                ("head_nodes", ctypes.c_int32), ("head_select", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,7 +68,7 @@ class fp_batch(ctypes.Structure):
 
 # every symbol include/forest_pack.h declares
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
-           "fp_predict_leaves", "fp_predict_batched", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
+           "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
            "fp_plain_release"]
 
@@ -95,6 +98,7 @@ def lib() -> ctypes.CDLL:
                 "fp_packed_image": ([P, ctypes.POINTER(i64)], P),
                 "fp_upload": ([P, P, ctypes.POINTER(P)], ctypes.c_int),
                 "fp_predict": ([P, P, i64, P, P, P], ctypes.c_int),
+                "fp_configure": ([P, ctypes.POINTER(fp_pack_params)], ctypes.c_int),
                 "fp_predict_leaves": ([P, P, i64, P, P], ctypes.c_int),
                 "fp_predict_batched": ([P, P, i32, P], ctypes.c_int),
                 "fp_sync_status": ([P, P], ctypes.c_int),
@@ -121,7 +125,8 @@ def fp_last_error() -> str:
 
 def _check(rc: int, what: str) -> None:
     if rc != FP_OK:
-        raise FPError(rc, f"{what}: {fp_last_error()}")
+        msg = fp_last_error()
+        raise FPError(rc, msg if msg.startswith(what) else f"{what}: {msg}")
 
 
 # ----------------------------------------------------------------- helpers
@@ -175,10 +180,12 @@ def _dptr(t, dtype, shape=None, name="tensor"):
 # ------------------------------------------------------------ C-ABI mirrors
 
 def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_tile: int = 0,
-                   warps_per_cta: int = 0, pass_bytes: int = 0) -> "PackedForest":
+                   warps_per_cta: int = 0, pass_bytes: int = 0, refill_lanes: int = 0,
+                   head_select: int = 0) -> "PackedForest":
     keep: list = []
     desc = make_desc(forest, keep)
-    params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes)
+    params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes, refill_lanes,
+                            head_select)
     out = ctypes.c_void_p()
     _check(lib().fp_pack_forest(ctypes.byref(desc), ctypes.byref(params), ctypes.byref(out)), "fp_pack_forest")
     return PackedForest(out.value, forest)
@@ -276,6 +283,14 @@ class DeviceForest:
         self.handle = handle
         i = fp_packed_info()
         _check(lib().fp_device_info_get(handle, ctypes.byref(i)), "fp_device_info_get")
+        self.info = i.as_dict()
+
+    def configure(self, obs_tile: int = 0, warps_per_cta: int = 0, refill_lanes: int = 0) -> None:
+        """Change launch parameters (fp_configure); layout stays as packed."""
+        params = fp_pack_params(0, -1, obs_tile, warps_per_cta, 0, refill_lanes, 0)
+        _check(lib().fp_configure(self.handle, ctypes.byref(params)), "fp_configure")
+        i = fp_packed_info()
+        _check(lib().fp_device_info_get(self.handle, ctypes.byref(i)), "fp_device_info_get")
         self.info = i.as_dict()
 
     def predict(self, X, votes: bool = True, classes: bool = True, stream=None):

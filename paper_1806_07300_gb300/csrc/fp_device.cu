@@ -27,8 +27,8 @@ struct fp_device_forest {
     uint8_t *d_image = nullptr;
     int32_t *d_status = nullptr;
     int32_t R = 0;            // observation tile actually launched (fits shared memory)
-    int32_t P = 0;            // shared-memory row stride (floats)
     int32_t threads = 0;
+    int32_t refill = 8;
     int32_t head_smem = 0;
     size_t smem_votes = 0, smem_leaves = 0;
     int32_t grid_votes = 0, grid_leaves = 0;  // resident CTAs for a persistent launch
@@ -67,9 +67,11 @@ int scratch_pool(int device, cudaMemPool_t *out) {
     return FP_OK;
 }
 
-size_t smem_bytes(int R, int P, int head_smem, int C, bool leaves) {
-    size_t xs = ((size_t)R * P * 4 + 15) & ~(size_t)15;
-    return xs + (size_t)head_smem + (leaves ? 0 : (size_t)R * C * 4);
+// rows tile (feature-major) + FP_NBUF bin blocks + votes + per-warp task rings
+size_t smem_bytes(int R, int F, int head_smem, int C, int warps, bool leaves) {
+    const size_t xs = ((size_t)R * F * 4 + 15) & ~(size_t)15;
+    const size_t votes = leaves ? 0 : (((size_t)R * C * 4 + 15) & ~(size_t)15);
+    return xs + FP_NBUF * (size_t)head_smem + votes + (size_t)warps * FP_RING * 8;
 }
 
 template <bool LEAVES>
@@ -91,28 +93,64 @@ int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
     return FP_OK;
 }
 
+// Fit the observation tile to shared memory and size the persistent grid.
+int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refill) {
+    if (tile < 32 || tile > 2048 || tile % 32 || warps < 1 || warps > 32 || refill < 1 || refill > 32) {
+        fp_set_error("launch parameters out of range (obs_tile %d, warps %d, refill %d)", tile, warps, refill);
+        return FP_EINVAL;
+    }
+    int max_optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const size_t budget = (size_t)max_optin - 64;  // static shared variables
+    const int C = f->hdr.n_classes, F = f->hdr.n_features;
+    int R = tile;
+    while (R > 32 && smem_bytes(R, F, f->head_smem, C, warps, false) > budget) R -= 32;
+    if (smem_bytes(R, F, f->head_smem, C, warps, false) > budget) {
+        fp_set_error("a 32-row tile, the bin-block buffers and the task rings need %zu bytes of shared memory (limit %zu)",
+                     smem_bytes(R, F, f->head_smem, C, warps, false), budget);
+        return FP_EUNSUPPORTED;
+    }
+    fp_device_forest g = *f;
+    g.R = R;
+    g.threads = 32 * warps;
+    g.refill = refill;
+    g.smem_votes = smem_bytes(R, F, f->head_smem, C, warps, false);
+    g.smem_leaves = smem_bytes(R, F, f->head_smem, C, warps, true);
+    int rc = configure<false>(&g, g.smem_votes, &g.grid_votes);
+    if (rc) return rc;
+    rc = configure<true>(&g, g.smem_leaves, &g.grid_leaves);
+    if (rc) return rc;
+    f->R = g.R;
+    f->threads = g.threads;
+    f->refill = g.refill;
+    f->smem_votes = g.smem_votes;
+    f->smem_leaves = g.smem_leaves;
+    f->grid_votes = g.grid_votes;
+    f->grid_leaves = g.grid_leaves;
+    return FP_OK;
+}
+
 TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     TravParams p;
     memset(&p, 0, sizeof p);
     const FpImageHeader &h = f->hdr;
-    p.deep = reinterpret_cast<const uint2 *>(f->d_image + h.off_deep);
+    p.deep = reinterpret_cast<const FpSuper *>(f->d_image + h.off_deep);
     p.heads = f->d_image + h.off_heads;
     p.bins = reinterpret_cast<const FpBin *>(f->d_image + h.off_bins);
     p.passes = reinterpret_cast<const FpPass *>(f->d_image + h.off_passes);
     p.tree_base = reinterpret_cast<const uint32_t *>(f->d_image + h.off_tree_base);
     p.pheads = reinterpret_cast<const int32_t *>(f->d_image + h.off_pheads);
-    p.deep_leaf = reinterpret_cast<const int2 *>(f->d_image + h.off_deep_leaf);
+    p.deep_leaf = reinterpret_cast<const int32_t *>(f->d_image + h.off_deep_leaf);
     p.X = X;
     p.n = n;
     p.F = h.n_features;
-    p.P = f->P;
     p.C = h.n_classes;
     p.T = h.n_trees;
-    p.S = h.slots;
-    p.Lk = h.links;
     p.R = f->R;
     p.n_tiles = (n + f->R - 1) / f->R;
     p.head_smem = f->head_smem;
+    p.refill = f->refill;
     p.status = f->d_status;
     return p;
 }
@@ -162,30 +200,9 @@ extern "C" int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_for
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(image)"); goto fail; }
     e = cudaStreamSynchronize(s);  // the caller may free the host image on return
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamSynchronize"); goto fail; }
-    {
-        f->P = h->n_features | 1;
-        f->threads = 32 * h->warps_per_cta;
-        f->head_smem = (h->max_head_bytes + 15) & ~15;
-        int max_optin = 0;
-        e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaDeviceGetAttribute"); goto fail; }
-        const size_t budget = (size_t)max_optin - 64;  // static shared variables
-        int R = h->obs_tile;
-        while (R > 32 && smem_bytes(R, f->P, f->head_smem, h->n_classes, false) > budget) R -= 32;
-        if (smem_bytes(R, f->P, f->head_smem, h->n_classes, false) > budget) {
-            fp_set_error("fp_upload: a 32-row tile and one bin block need %zu bytes of shared memory (limit %zu)",
-                         smem_bytes(R, f->P, f->head_smem, h->n_classes, false), budget);
-            rc = FP_EUNSUPPORTED;
-            goto fail;
-        }
-        f->R = R;
-        f->smem_votes = smem_bytes(R, f->P, f->head_smem, h->n_classes, false);
-        f->smem_leaves = smem_bytes(R, f->P, f->head_smem, h->n_classes, true);
-        rc = configure<false>(f, f->smem_votes, &f->grid_votes);
-        if (rc) goto fail;
-        rc = configure<true>(f, f->smem_leaves, &f->grid_leaves);
-        if (rc) goto fail;
-    }
+    f->head_smem = (h->max_head_bytes + 15) & ~15;
+    rc = launch_setup(f, h->obs_tile, h->warps_per_cta, h->refill_lanes);
+    if (rc) goto fail;
     *out = f;
     return FP_OK;
 fail:
@@ -193,6 +210,25 @@ fail:
     if (f->d_status) cudaFree(f->d_status);
     delete f;
     return rc;
+}
+
+extern "C" int fp_configure(fp_device_forest *f, const fp_pack_params *params) {
+    if (!f || !params) {
+        fp_set_error("fp_configure: NULL argument");
+        return FP_EINVAL;
+    }
+    const FpImageHeader &h = f->hdr;
+    if ((params->bin_size && params->bin_size != h.bin_size) ||
+        (params->interleave_depth > 0 && params->interleave_depth != h.depth) ||
+        (params->pass_bytes && params->pass_bytes != h.pass_bytes)) {
+        fp_set_error("fp_configure: layout parameters can only change by packing again");
+        return FP_EINVAL;
+    }
+    int rc = check_device(f);
+    if (rc) return rc;
+    return launch_setup(f, params->obs_tile ? params->obs_tile : f->R,
+                        params->warps_per_cta ? params->warps_per_cta : f->threads / 32,
+                        params->refill_lanes ? params->refill_lanes : f->refill);
 }
 
 extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, uint32_t *out_votes,
@@ -293,6 +329,8 @@ extern "C" int fp_device_info_get(const fp_device_forest *f, fp_packed_info *inf
     }
     fp_fill_info(&f->hdr, info);
     info->obs_tile = f->R;
+    info->warps_per_cta = f->threads / 32;
+    info->refill_lanes = f->refill;
     return FP_OK;
 }
 

@@ -1,64 +1,76 @@
 // fp_internal.h -- the packed image format shared by the host packer and the
 // device code of the library (not part of the public C ABI).
 //
-// Image = one contiguous, 256-byte-aligned blob, uploaded verbatim:
+// Image = one contiguous blob, sections 256-byte aligned, uploaded verbatim:
 //
 //   FpImageHeader
 //   FpBin    bins[n_bins]        bin b holds trees [first_tree, first_tree+width)
 //   FpPass   passes[n_passes]    pass p sweeps bins [bin_begin, bin_end)
-//   uint32   tree_base[T]        first deep record of each tree (index into deep)
-//   heads                        per bin, 16-byte aligned, one block of
-//                                  S*width head records (8 B), slot-major:
-//                                    head[s*width + k] = BFS slot s of tree k
-//                                  then L*width link entries (4 B), likewise
-//                                    link[j*width + k] = slot S+j of tree k
-//   deep     uint2 records       per tree, hot-first depth-first order
+//   uint32   tree_base[T]        first super-node of each tree (index into deep)
+//   blocks                       per bin, 16-byte aligned, the interleaved block
+//                                of the bin's trees (stride = width | 1, odd):
+//                                  nranks*stride head nodes (8 B), rank-major:
+//                                    node[rank*stride + k] = rank-th head node of tree k
+//                                  nexits*stride exit references (4 B):
+//                                    exit[e*stride + k]   = e-th exit of tree k
+//   deep     FpSuper[]           per tree, its super-nodes in Stat order
 //   --- end of the classification part (class_bytes) ---
-//   parity heads                 per bin, int32 leaf ids mirroring the head
-//                                block (S*width, then L*width entries)
-//   deep_leaf int2               per deep record: leaf id of the left / right
-//                                child when that child is a leaf, else -1
+//   parity blocks                per bin, int32 leaf id of each exit (or -1),
+//                                [nexits][stride] like the exits
+//   deep_leaf int32[4] per super-node: leaf id behind each exit, or -1
 //
-// S = 2^(d+1) - 1 implicit breadth-first slots cover levels 0..d (children of
-// slot s are 2s+1 and 2s+2); L = 2^(d+1) link entries cover level d+1.
+// Head of a tree: the K = 2^(d+1) - 1 internal nodes of highest training
+// cardinality (ties: shallower, then earlier), a subtree that contains the
+// root; for a complete tree these are exactly levels 0..d.  They are ranked
+// in depth-first order that visits the more frequently reached child first.
 //
-// Head record {float thr; uint32 meta}:
-//   meta bit 31 = 0: internal node, meta = feature
-//   meta bit 31 = 1: leaf, meta & 0x7FFFFFFF = class (0x7FFFFFFF: empty slot)
-// Link entry (uint32):
-//   bit 31 = 1: leaf, low bits = class (0x7FFFFFFF: empty)
-//   bit 31 = 0: tree-local index of the deep record of that node
-// Deep record {float thr; uint32 meta}:
+// Head node {float thr; uint32 meta}:
 //   [31:22] feature
-//   [21]    hot child is the right child (the hot child sits at index + 1)
-//   [20]    cold child is a leaf: [18:0] = its class
-//   [19]    both children are leaves: [8:0] left class, [17:9] right class
-//   [18:0]  otherwise: tree-local index of the cold child's record
+//   [21:11] right target, [10:0] left target: a target below the bin's
+//           nranks is the rank of a head node, otherwise it names
+//           exit[target - nranks]
+// A tree whose root is a leaf gets one head node whose two targets both name
+// an exit holding that leaf.  nranks + nexits <= 2048 (so d <= 9).
+//
+// A reference (exit entry or super-node exit) is a uint32:
+//   bit 31 = 1: a leaf, bits 30..0 = its class
+//   bit 31 = 0: a tree-local super-node index
+//
+// Super-node (32 bytes, one L2 sector, 32-byte aligned): a node v below the
+// head together with its two children, i.e. two levels of the tree resolved
+// by one load:
+//   w[0] threshold of v            w[1] threshold of v's left child
+//   w[2] threshold of v's right child
+//   w[3] features: v [9:0], left child [19:10], right child [29:20]
+//   w[4..7] exits: (left,left) (left,right) (right,left) (right,right)
+// A child that is a leaf keeps a dummy split and both of its exits name the
+// leaf, so either outcome of the dummy compare lands on it.
 #pragma once
 #include <stdint.h>
 
 #define FP_IMAGE_MAGIC 0x4B435046u /* "FPCK" */
-#define FP_IMAGE_VERSION 1u
+#define FP_IMAGE_VERSION 4u
 
-#define FP_META_FEATURE_SHIFT 22
-#define FP_META_HOT_RIGHT (1u << 21)
-#define FP_META_COLD_LEAF (1u << 20)
-#define FP_META_BOTH_LEAF (1u << 19)
-#define FP_META_PAYLOAD_MASK 0x7FFFFu
-#define FP_MAX_DEEP_PER_TREE (1 << 19)
 #define FP_MAX_FEATURES 1024
 #define FP_MAX_CLASSES 512
-#define FP_HEAD_LEAF 0x80000000u
-#define FP_HEAD_EMPTY 0xFFFFFFFFu
+#define FP_REF_LEAF 0x80000000u
 #define FP_MAX_DEPTH 9
+#define FP_TARGET_BITS 11
+#define FP_TARGET_MASK 2047u
+
+struct FpSuper {
+    uint32_t w[8];
+};
 
 struct FpBin {
-    uint32_t head_off;    // bytes from the start of the heads section
-    uint32_t head_bytes;  // head records + link entries, padded to 16 B
+    uint32_t head_off;    // bytes from the start of the blocks section
+    uint32_t head_bytes;  // head nodes + exits, padded to 16 B
     int32_t first_tree;
     int32_t width;
-    uint32_t phead_off;   // bytes from the start of the parity-heads section
-    uint32_t pad[3];
+    uint32_t phead_off;   // bytes from the start of the parity-blocks section
+    int32_t stride;       // width | 1
+    int32_t nranks;       // head node rows
+    int32_t nexits;       // exit rows
 };
 
 struct FpPass {
@@ -69,13 +81,16 @@ struct FpImageHeader {
     uint32_t magic, version;
     int32_t n_trees, n_features, n_classes;
     int32_t bin_size, depth, n_bins, n_passes;
-    int32_t slots, links;          // S and L
+    int32_t head_nodes;            // K, head nodes per tree at most
+    int32_t head_select;           // 0: highest cardinality, 1: complete levels 0..d
     int32_t obs_tile, warps_per_cta;
     int32_t max_head_bytes;
-    int64_t n_deep;
+    int32_t refill_lanes;
+    int64_t n_super;               // super-nodes in the deep section
     int64_t off_bins, off_passes, off_tree_base, off_heads, off_deep;
     int64_t off_pheads, off_deep_leaf;
     int64_t class_bytes;           // end of the classification part
     int64_t total_bytes;           // end of the image (incl. parity tables)
     int64_t head_bytes_total, pass_bytes;
+    int64_t n_internal;            // internal nodes of the forest
 };

@@ -1,19 +1,23 @@
 // fp_pack.cpp -- host layout builder: trained forest -> packed image.
 //
-// Implements the layout of Section III-A of the paper, adapted to 8-byte
-// records and a GPU that stages each bin's interleaved block in shared memory:
-//   DF-  (Section III-A): leaves are not stored; the parent record carries the
-//        leaf's class (the paper's shared per-class nodes, folded into the
-//        parent so no extra load is spent on them);
-//   Stat (Section III-A): below the interleaved levels each tree is laid out
-//        depth-first with the child of larger training cardinality placed
-//        immediately after its parent (left on ties); when one child is a leaf
-//        the internal child is the adjacent one;
+// Implements the layout of Section III-A of the paper for a GPU that stages
+// each bin's interleaved block in shared memory and reads the rest of a tree
+// in 32-byte sectors:
 //   Bin  (Section III-A, Fig. 2, Fig. 3): trees [bB, (b+1)B) form bin b; the
-//        nodes of levels 0..d of the bin's trees are interleaved slot by slot
-//        (head[s*width + k]), so the roots of all trees of a bin are
-//        contiguous (Fig. 2: depth 0 = roots only); level d+1 is a row of
-//        4-byte links into each tree's Stat region.
+//        heads of the bin's trees -- the 2^(d+1)-1 most frequently visited
+//        nodes of each tree, which for a complete tree are levels 0..d -- are
+//        interleaved rank by rank (node[rank*stride + k]), so the roots of
+//        all trees of a bin are contiguous (Fig. 2: depth 0 = roots only) and
+//        the block is staged into shared memory in one piece;
+//   DF-  (Section III-A): leaves are not stored as nodes; a reference to a
+//        leaf carries its class (the paper's shared per-class nodes, folded
+//        into the reference so no load is spent on them);
+//   Stat (Section III-A): below the interleaved levels a tree is cut into
+//        super-nodes of two levels (a node and its two children: one 32-byte
+//        sector, one load) laid out depth-first with the child super-node of
+//        largest training cardinality immediately after its parent -- the
+//        paper's "more likely path adjacent" rule at the granularity of the
+//        GPU's memory transaction.
 // The image format is described in fp_internal.h.
 #include <algorithm>
 #include <cstdio>
@@ -109,76 +113,164 @@ int validate_tree(const TreeRef &t, int32_t F, int32_t C, int32_t ti, std::vecto
     return FP_OK;
 }
 
-// Stat rule: is the right child the hot (adjacent) one?
-bool hot_is_right(const TreeRef &t, int32_t v) {
-    int32_t l = t.L[v], r = t.R[v];
-    bool li = !t.leaf(l), ri = !t.leaf(r);
-    if (li != ri) return ri;
-    if (!t.Card) return false;
-    return t.Card[r] > t.Card[l];
-}
-
 struct TreeLayout {
-    // head: node id per BFS slot (-1 = empty) for slots 0..S+L-1
-    std::vector<int32_t> slot_node;
-    // deep: node ids in record order
-    std::vector<int32_t> deep_nodes;
-    std::vector<int32_t> deep_index;  // node id -> record index (-1 if not deep)
+    std::vector<int32_t> head;       // node id per head rank
+    std::vector<uint32_t> head_meta; // unused (kept zero); targets are encoded per bin
+    std::vector<int32_t> rank;       // node id -> head rank (-1 outside the head)
+    std::vector<int32_t> exits;      // node id behind each exit (leaf or deep root)
+    std::vector<int32_t> sn_root;    // root node of each super-node, in layout order
+    std::vector<int32_t> sn_index;   // node id -> super-node index (-1 if it roots none)
 };
 
-int layout_tree(const TreeRef &t, int32_t d, int32_t S, int32_t Lk, TreeLayout &out, int32_t ti) {
-    out.slot_node.assign((size_t)(S + Lk), -1);
-    out.slot_node[0] = 0;
-    for (int32_t s = 0; s < S; ++s) {
-        int32_t v = out.slot_node[s];
-        if (v < 0 || t.leaf(v)) continue;
-        out.slot_node[2 * s + 1] = t.L[v];
-        out.slot_node[2 * s + 2] = t.R[v];
+// The four exits of the super-node rooted at v: the grandchildren through
+// internal children, or the leaf child itself (twice).
+void super_exits(const TreeRef &t, int32_t v, int32_t e[4]) {
+    const int32_t l = t.L[v], r = t.R[v];
+    if (t.leaf(l)) { e[0] = e[1] = l; } else { e[0] = t.L[l]; e[1] = t.R[l]; }
+    if (t.leaf(r)) { e[2] = e[3] = r; } else { e[2] = t.L[r]; e[3] = t.R[r]; }
+}
+
+int64_t card_of(const TreeRef &t, int32_t v) { return t.Card ? t.Card[v] : 0; }
+
+int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti);
+
+// Head: the K internal nodes of highest training cardinality (ties:
+// shallower, then lower node id) -- the most popular paths of Section III-A,
+// kept in fast memory -- or, when select_levels is set, the internal nodes of
+// levels 0..d.  Both sets contain every ancestor of their members.  They are
+// ranked depth-first, more frequently reached child first (Stat), so the
+// first child visited inside the head sits at the next rank.  Below the head
+// the tree is cut into super-nodes (a node and its two children: one 32-byte
+// sector, one load) laid out depth-first with the child super-node of largest
+// cardinality right after its parent (Stat at super-node granularity).
+int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, TreeLayout &out, int32_t ti) {
+    const int32_t m = (int32_t)t.m;
+    std::vector<int32_t> depth((size_t)m, 0);
+    std::vector<int32_t> order;  // breadth-first
+    order.reserve((size_t)m);
+    order.push_back(0);
+    for (size_t i = 0; i < order.size(); ++i) {
+        const int32_t v = order[i];
+        if (t.leaf(v)) continue;
+        depth[t.L[v]] = depth[v] + 1;
+        depth[t.R[v]] = depth[v] + 1;
+        order.push_back(t.L[v]);
+        order.push_back(t.R[v]);
     }
-    out.deep_index.assign((size_t)t.m, -1);
-    out.deep_nodes.clear();
-    // deep roots: internal nodes at level d+1, in link order; each subtree in
-    // hot-first pre-order (explicit stack: hot child pops first)
+    std::vector<uint8_t> in_head((size_t)m, 0);
+    if (!t.leaf(0)) {
+        std::vector<int32_t> cand;
+        for (int32_t v : order)
+            if (!t.leaf(v) && (!select_levels || depth[v] <= d)) cand.push_back(v);
+        if (!select_levels) {
+            std::stable_sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                const int64_t ca = card_of(t, a), cb = card_of(t, b);
+                if (ca != cb) return ca > cb;
+                if (depth[a] != depth[b]) return depth[a] < depth[b];
+                return a < b;
+            });
+            if ((int64_t)cand.size() > K) cand.resize((size_t)K);
+        }
+        // members reached from the root through members form the head (with
+        // consistent cardinalities that is every member)
+        for (int32_t v : cand) in_head[v] = 1;
+    }
+    // children of v ordered for Stat: larger cardinality first, left on ties
+    auto kids_hot_first = [&](int32_t v, int32_t k[2]) {
+        const int32_t l = t.L[v], r = t.R[v];
+        const bool right_first = card_of(t, r) > card_of(t, l);
+        k[0] = right_first ? r : l;
+        k[1] = right_first ? l : r;
+    };
+    out.head.clear();
+    out.head_meta.clear();
+    out.exits.clear();
+    if (t.leaf(0)) {
+        // a single-leaf tree: one node whose two targets name one exit holding the leaf
+        out.head.push_back(0);
+        out.exits.push_back(0);
+        out.head_meta.push_back(0);  // targets are fixed up once the bin's nranks is known
+        return finish_super(t, out, ti);
+    }
+    std::vector<int32_t> rank((size_t)m, -1);
+    std::vector<int32_t> stack{0};
+    while (!stack.empty()) {
+        const int32_t v = stack.back();
+        stack.pop_back();
+        rank[v] = (int32_t)out.head.size();
+        out.head.push_back(v);
+        int32_t k[2];
+        kids_hot_first(v, k);
+        if (in_head[k[1]]) stack.push_back(k[1]);
+        if (in_head[k[0]]) stack.push_back(k[0]);
+    }
+    // children outside the head become exits, in rank order
+    out.head_meta.assign(out.head.size(), 0);
+    for (size_t i = 0; i < out.head.size(); ++i) {
+        const int32_t v = out.head[i];
+        for (int32_t c : {t.L[v], t.R[v]})
+            if (t.leaf(c) || !in_head[c]) out.exits.push_back(c);
+    }
+    if (out.head.size() + out.exits.size() > (size_t)FP_TARGET_MASK + 1) {
+        fp_set_error("tree %d: head of %zu nodes and %zu exits exceeds the 11-bit targets", ti, out.head.size(),
+                     out.exits.size());
+        return FP_EUNSUPPORTED;
+    }
+    out.rank = rank;
+    return finish_super(t, out, ti);
+}
+
+// Super-nodes below the head, rooted at the internal exits: depth-first,
+// the child super-node of largest cardinality right after its parent.
+int finish_super(const TreeRef &t, TreeLayout &out, int32_t ti) {
+    const int32_t m = (int32_t)t.m;
+    out.sn_index.assign((size_t)m, -1);
+    out.sn_root.clear();
     std::vector<int32_t> stack;
-    for (int32_t j = 0; j < Lk; ++j) {
-        int32_t root = out.slot_node[S + j];
-        if (root < 0 || t.leaf(root)) continue;
+    for (int32_t root : out.exits) {
+        if (t.leaf(root) || out.sn_index[root] >= 0) continue;
         stack.push_back(root);
         while (!stack.empty()) {
-            int32_t v = stack.back();
+            const int32_t v = stack.back();
             stack.pop_back();
-            out.deep_index[v] = (int32_t)out.deep_nodes.size();
-            out.deep_nodes.push_back(v);
-            bool hr = hot_is_right(t, v);
-            int32_t hot = hr ? t.R[v] : t.L[v], cold = hr ? t.L[v] : t.R[v];
-            if (!t.leaf(cold)) stack.push_back(cold);
-            if (!t.leaf(hot)) stack.push_back(hot);
+            out.sn_index[v] = (int32_t)out.sn_root.size();
+            out.sn_root.push_back(v);
+            int32_t e[4];
+            super_exits(t, v, e);
+            int32_t kids[4];
+            int nk = 0;
+            for (int q = 0; q < 4; ++q)
+                if (!t.leaf(e[q])) kids[nk++] = e[q];
+            if (t.Card)
+                std::stable_sort(kids, kids + nk, [&](int32_t a, int32_t b) { return t.Card[a] > t.Card[b]; });
+            for (int q = nk - 1; q >= 0; --q) stack.push_back(kids[q]);
         }
     }
-    if ((int64_t)out.deep_nodes.size() >= FP_MAX_DEEP_PER_TREE) {
-        fp_set_error("tree %d holds %zu records below the interleaved levels; the record format addresses %d",
-                     ti, out.deep_nodes.size(), FP_MAX_DEEP_PER_TREE - 1);
+    if ((int64_t)out.sn_root.size() >= (int64_t)FP_REF_LEAF) {
+        fp_set_error("tree %d needs more than 2^31 super-nodes", ti);
         return FP_EUNSUPPORTED;
     }
     return FP_OK;
 }
 
-uint32_t encode_deep(const TreeRef &t, const TreeLayout &lay, int32_t v) {
-    int32_t l = t.L[v], r = t.R[v];
-    uint32_t meta = (uint32_t)t.Fe[v] << FP_META_FEATURE_SHIFT;
-    if (t.leaf(l) && t.leaf(r)) {
-        meta |= FP_META_BOTH_LEAF | (uint32_t)t.Cl[l] | ((uint32_t)t.Cl[r] << 9);
-        return meta;
+uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v) {
+    return t.leaf(v) ? (FP_REF_LEAF | (uint32_t)t.Cl[v]) : (uint32_t)lay.sn_index[v];
+}
+
+void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, FpSuper &sn, int32_t leaf_ids[4]) {
+    const int32_t l = t.L[v], r = t.R[v];
+    float th0 = t.Th[v], th1 = t.leaf(l) ? 0.0f : t.Th[l], th2 = t.leaf(r) ? 0.0f : t.Th[r];
+    memcpy(&sn.w[0], &th0, 4);
+    memcpy(&sn.w[1], &th1, 4);
+    memcpy(&sn.w[2], &th2, 4);
+    const uint32_t fl = t.leaf(l) ? 0u : (uint32_t)t.Fe[l], fr = t.leaf(r) ? 0u : (uint32_t)t.Fe[r];
+    sn.w[3] = (uint32_t)t.Fe[v] | (fl << 10) | (fr << 20);
+    int32_t e[4];
+    super_exits(t, v, e);
+    for (int q = 0; q < 4; ++q) {
+        sn.w[4 + q] = ref_of(t, lay, e[q]);
+        leaf_ids[q] = t.leaf(e[q]) ? e[q] : -1;
     }
-    bool hr = hot_is_right(t, v);
-    int32_t cold = hr ? l : r;
-    if (hr) meta |= FP_META_HOT_RIGHT;
-    if (t.leaf(cold)) {
-        meta |= FP_META_COLD_LEAF | (uint32_t)t.Cl[cold];
-    } else {
-        meta |= (uint32_t)lay.deep_index[cold];
-    }
-    return meta;
 }
 
 }  // namespace
@@ -195,7 +287,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         return FP_EINVAL;
     }
     const int32_t T = desc->n_trees, F = desc->n_features, C = desc->n_classes;
-    if (T < 1 || T > (1 << 24) || F < 1 || F > FP_MAX_FEATURES || C < 1 || C > FP_MAX_CLASSES) {
+    if (T < 1 || T > (1 << 20) || F < 1 || F > FP_MAX_FEATURES || C < 1 || C > FP_MAX_CLASSES) {
         fp_set_error("fp_pack_forest: n_trees %d, n_features %d (1..%d), n_classes %d (1..%d)", T, F,
                      FP_MAX_FEATURES, C, FP_MAX_CLASSES);
         return (F > FP_MAX_FEATURES || C > FP_MAX_CLASSES) ? FP_EUNSUPPORTED : FP_EINVAL;
@@ -204,25 +296,27 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         fp_set_error("fp_pack_forest: tree_node_begin[0] must be 0");
         return FP_EINVAL;
     }
-    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0};
-    int32_t B = p.bin_size ? p.bin_size : std::min(T, 32);
-    int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 4;
-    int32_t W = p.warps_per_cta ? p.warps_per_cta : 8;
-    const int32_t P = F | 1;  // shared-memory row stride in floats (odd: no bank conflicts on one feature)
+    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0};
+    const int32_t refill = p.refill_lanes ? p.refill_lanes : 32;
+    int32_t B = p.bin_size ? p.bin_size : 1;
+    const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
+    const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
+    const bool select_levels = p.head_select == 1;
     int32_t R = p.obs_tile;
-    if (R == 0) {
-        int64_t r = (32 * 1024) / ((int64_t)P * 4);
+    if (R == 0) {  // rows take up to ~96 KiB of shared memory
+        int64_t r = (96 * 1024) / ((int64_t)F * 4);
         r = r / 32 * 32;
         R = (int32_t)std::max<int64_t>(32, std::min<int64_t>(1024, r));
     }
-    int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
-    if (B < 1 || B > 1024 || d < 0 || d > FP_MAX_DEPTH || W < 1 || W > 32 || R < 32 || R > 2048 || R % 32) {
-        fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d)", B, d, R,
-                     W);
+    const int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
+    if (B < 1 || B > 1024 || d < 0 || d > FP_MAX_DEPTH || W < 1 || W > 32 || R < 32 || R > 2048 || R % 32 ||
+        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 1) {
+        fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
+                     "refill %d, head_select %d)", B, d, R, W, refill, p.head_select);
         return FP_EINVAL;
     }
     if (B > T) B = T;
-    const int32_t S = (1 << (d + 1)) - 1, Lk = 1 << (d + 1);
+    const int32_t K = (1 << (d + 1)) - 1;
     const int32_t n_bins = (T + B - 1) / B;
 
     try {
@@ -230,6 +324,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         std::vector<TreeLayout> lays((size_t)T);
         std::vector<uint8_t> seen;
         std::vector<int64_t> deep_count((size_t)T);
+        int64_t n_internal = 0;
         for (int32_t t = 0; t < T; ++t) {
             int64_t b = desc->tree_node_begin[t], e = desc->tree_node_begin[t + 1];
             if (e < b) {
@@ -240,9 +335,10 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                        desc->cardinality ? desc->cardinality + b : nullptr, e - b};
             int rc = validate_tree(tr, F, C, t, seen);
             if (rc) return rc;
-            rc = layout_tree(tr, d, S, Lk, lays[t], t);
+            rc = layout_tree(tr, K, d, select_levels, lays[t], t);
             if (rc) return rc;
-            deep_count[t] = (int64_t)lays[t].deep_nodes.size();
+            deep_count[t] = (int64_t)lays[t].sn_root.size();
+            for (int64_t v = 0; v < tr.m; ++v) n_internal += !tr.leaf((int32_t)v);
         }
 
         // ---- section sizes
@@ -252,8 +348,10 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.version = FP_IMAGE_VERSION;
         h.n_trees = T; h.n_features = F; h.n_classes = C;
         h.bin_size = B; h.depth = d; h.n_bins = n_bins;
-        h.slots = S; h.links = Lk;
+        h.head_nodes = K;
+        h.head_select = select_levels ? 1 : 0;
         h.obs_tile = R; h.warps_per_cta = W;
+        h.refill_lanes = refill;
         std::vector<FpBin> bins((size_t)n_bins);
         int64_t head_total = 0, phead_total = 0;
         int32_t max_head = 0;
@@ -262,8 +360,18 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             memset(&bn, 0, sizeof bn);
             bn.first_tree = b * B;
             bn.width = std::min(B, T - b * B);
-            int64_t bytes = align_up((int64_t)S * bn.width * 8 + (int64_t)Lk * bn.width * 4, 16);
-            if (head_total + bytes > UINT32_MAX || bytes > 160 * 1024) {
+            bn.stride = bn.width | 1;
+            for (int32_t k = 0; k < bn.width; ++k) {
+                bn.nranks = std::max<int32_t>(bn.nranks, (int32_t)lays[bn.first_tree + k].head.size());
+                bn.nexits = std::max<int32_t>(bn.nexits, (int32_t)lays[bn.first_tree + k].exits.size());
+            }
+            if (bn.nranks + bn.nexits > (int32_t)FP_TARGET_MASK + 1) {
+                fp_set_error("fp_pack_forest: bin %d needs %d head targets (at most %u); lower interleave_depth", b,
+                             bn.nranks + bn.nexits, FP_TARGET_MASK + 1);
+                return FP_EUNSUPPORTED;
+            }
+            const int64_t bytes = align_up((int64_t)bn.nranks * bn.stride * 8 + (int64_t)bn.nexits * bn.stride * 4, 16);
+            if (head_total + bytes > UINT32_MAX || bytes > 100 * 1024) {
                 fp_set_error("fp_pack_forest: interleaved block of %lld bytes per bin is too large; lower "
                              "bin_size or interleave_depth", (long long)bytes);
                 return FP_EUNSUPPORTED;
@@ -272,15 +380,14 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             bn.head_bytes = (uint32_t)bytes;
             head_total += bytes;
             max_head = std::max<int32_t>(max_head, (int32_t)bytes);
-            int64_t pbytes = align_up((int64_t)(S + Lk) * bn.width * 4, 16);
             bn.phead_off = (uint32_t)phead_total;
-            phead_total += pbytes;
+            phead_total += align_up((int64_t)bn.nexits * bn.stride * 4, 16);
         }
         std::vector<int64_t> tree_base((size_t)T + 1, 0);
         for (int32_t t = 0; t < T; ++t) tree_base[t + 1] = tree_base[t] + deep_count[t];
         const int64_t n_deep = tree_base[T];
         if (n_deep > (int64_t)UINT32_MAX) {
-            fp_set_error("fp_pack_forest: %lld deep records exceed the 32-bit tree base", (long long)n_deep);
+            fp_set_error("fp_pack_forest: %lld super-nodes exceed the 32-bit tree base", (long long)n_deep);
             return FP_EUNSUPPORTED;
         }
         // passes: consecutive bins whose records fit the budget
@@ -289,8 +396,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             int32_t b0 = 0;
             int64_t acc = 0;
             for (int32_t b = 0; b < n_bins; ++b) {
-                int64_t bytes = bins[b].head_bytes +
-                                8 * (tree_base[bins[b].first_tree + bins[b].width] - tree_base[bins[b].first_tree]);
+                int64_t bytes = bins[b].head_bytes + (int64_t)sizeof(FpSuper) *
+                                (tree_base[bins[b].first_tree + bins[b].width] - tree_base[bins[b].first_tree]);
                 if (pass_budget > 0 && b > b0 && acc + bytes > pass_budget) {
                     passes.push_back({b0, b});
                     b0 = b;
@@ -302,7 +409,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         }
         h.n_passes = (int32_t)passes.size();
         h.max_head_bytes = max_head;
-        h.n_deep = n_deep;
+        h.n_super = n_deep;
+        h.n_internal = n_internal;
         h.head_bytes_total = head_total;
         h.pass_bytes = pass_budget;
 
@@ -311,10 +419,10 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.off_passes = off; off = align_up(off + (int64_t)sizeof(FpPass) * h.n_passes, 256);
         h.off_tree_base = off; off = align_up(off + 4 * (int64_t)T, 256);
         h.off_heads = off; off = align_up(off + head_total, 256);
-        h.off_deep = off; off = align_up(off + 8 * n_deep, 256);
+        h.off_deep = off; off = align_up(off + (int64_t)sizeof(FpSuper) * n_deep, 256);
         h.class_bytes = off;
         h.off_pheads = off; off = align_up(off + phead_total, 256);
-        h.off_deep_leaf = off; off = align_up(off + 8 * n_deep, 256);
+        h.off_deep_leaf = off; off = align_up(off + 16 * n_deep, 256);
         h.total_bytes = off;
 
         auto *pf = new fp_packed_forest;
@@ -327,53 +435,56 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         uint32_t *tb = reinterpret_cast<uint32_t *>(img + h.off_tree_base);
         for (int32_t t = 0; t < T; ++t) tb[t] = (uint32_t)tree_base[t];
 
-        // ---- heads (interleaved, slot-major) and their parity mirror
+        // ---- interleaved blocks (rank-major across the bin's trees) and their parity mirror
         for (int32_t b = 0; b < n_bins; ++b) {
             const FpBin &bn = bins[b];
             uint8_t *blk = img + h.off_heads + bn.head_off;
-            uint32_t *link = reinterpret_cast<uint32_t *>(blk + (int64_t)S * bn.width * 8);
-            int32_t *phead = reinterpret_cast<int32_t *>(img + h.off_pheads + bn.phead_off);
+            uint32_t *exits = reinterpret_cast<uint32_t *>(blk + (int64_t)bn.nranks * bn.stride * 8);
+            int32_t *pexits = reinterpret_cast<int32_t *>(img + h.off_pheads + bn.phead_off);
+            for (int64_t i = 0; i < (int64_t)bn.nexits * bn.stride; ++i) {
+                exits[i] = FP_REF_LEAF | 0x7FFFFFFFu;  // unused entries name no class
+                pexits[i] = -1;
+            }
             for (int32_t k = 0; k < bn.width; ++k) {
                 const int32_t t = bn.first_tree + k;
                 const int64_t nb = desc->tree_node_begin[t];
                 TreeRef tr{desc->left + nb, desc->right + nb, desc->feature + nb, desc->leaf_class + nb,
                            desc->threshold + nb, nullptr, desc->tree_node_begin[t + 1] - nb};
                 const TreeLayout &lay = lays[t];
-                for (int32_t s = 0; s < S; ++s) {
-                    int32_t v = lay.slot_node[s];
+                // exit index of each (node, side), in the order layout_tree made them
+                size_t next_exit = 0;
+                for (size_t i = 0; i < lay.head.size(); ++i) {
+                    const int32_t v = lay.head[i];
                     float thr = 0.0f;
-                    uint32_t meta = FP_HEAD_EMPTY;
-                    int32_t leaf_id = -1;
-                    if (v >= 0 && tr.leaf(v)) {
-                        meta = FP_HEAD_LEAF | (uint32_t)tr.Cl[v];
-                        leaf_id = v;
-                    } else if (v >= 0) {
+                    uint32_t meta, tgt[2];
+                    if (tr.leaf(v)) {  // single-leaf tree
+                        tgt[0] = tgt[1] = (uint32_t)bn.nranks;
+                        meta = 0;
+                    } else {
                         thr = tr.Th[v];
-                        meta = (uint32_t)tr.Fe[v];
+                        meta = (uint32_t)tr.Fe[v] << 22;
+                        const int32_t c2[2] = {tr.L[v], tr.R[v]};
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            const int32_t c = c2[s2];
+                            tgt[s2] = (!tr.leaf(c) && lay.rank[c] >= 0) ? (uint32_t)lay.rank[c]
+                                                                         : (uint32_t)(bn.nranks + next_exit++);
+                        }
                     }
-                    uint8_t *rec = blk + ((int64_t)s * bn.width + k) * 8;
+                    meta |= (tgt[1] << FP_TARGET_BITS) | tgt[0];
+                    uint8_t *rec = blk + ((int64_t)i * bn.stride + k) * 8;
                     memcpy(rec, &thr, 4);
                     memcpy(rec + 4, &meta, 4);
-                    phead[(int64_t)s * bn.width + k] = leaf_id;
                 }
-                for (int32_t j = 0; j < Lk; ++j) {
-                    int32_t v = lay.slot_node[S + j];
-                    uint32_t e = FP_HEAD_EMPTY;
-                    int32_t leaf_id = -1;
-                    if (v >= 0 && tr.leaf(v)) {
-                        e = FP_HEAD_LEAF | (uint32_t)tr.Cl[v];
-                        leaf_id = v;
-                    } else if (v >= 0) {
-                        e = (uint32_t)lay.deep_index[v];
-                    }
-                    link[(int64_t)j * bn.width + k] = e;
-                    phead[(int64_t)(S + j) * bn.width + k] = leaf_id;
+                for (size_t e = 0; e < lay.exits.size(); ++e) {
+                    const int32_t v = lay.exits[e];
+                    exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v);
+                    pexits[(int64_t)e * bn.stride + k] = tr.leaf(v) ? v : -1;
                 }
             }
         }
 
-        // ---- deep records and leaf-id side table
-        uint8_t *deep = img + h.off_deep;
+        // ---- super-nodes and their leaf-id side table
+        FpSuper *deep = reinterpret_cast<FpSuper *>(img + h.off_deep);
         int32_t *dleaf = reinterpret_cast<int32_t *>(img + h.off_deep_leaf);
         for (int32_t t = 0; t < T; ++t) {
             const int64_t nb = desc->tree_node_begin[t];
@@ -381,15 +492,9 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                        desc->threshold + nb, desc->cardinality ? desc->cardinality + nb : nullptr,
                        desc->tree_node_begin[t + 1] - nb};
             const TreeLayout &lay = lays[t];
-            for (size_t i = 0; i < lay.deep_nodes.size(); ++i) {
-                int32_t v = lay.deep_nodes[i];
-                float thr = tr.Th[v];
-                uint32_t meta = encode_deep(tr, lay, v);
-                int64_t g = tree_base[t] + (int64_t)i;
-                memcpy(deep + g * 8, &thr, 4);
-                memcpy(deep + g * 8 + 4, &meta, 4);
-                dleaf[2 * g] = tr.leaf(tr.L[v]) ? tr.L[v] : -1;
-                dleaf[2 * g + 1] = tr.leaf(tr.R[v]) ? tr.R[v] : -1;
+            for (size_t i = 0; i < lay.sn_root.size(); ++i) {
+                const int64_t g = tree_base[t] + (int64_t)i;
+                encode_super(tr, lay, lay.sn_root[i], deep[g], dleaf + 4 * g);
             }
         }
         *out = pf;
@@ -419,16 +524,20 @@ void fp_fill_info(const FpImageHeader *h, fp_packed_info *info) {
     info->n_classes = h->n_classes;
     info->bin_size = h->bin_size;
     info->interleave_depth = h->depth;
+    info->head_nodes = h->head_nodes;
+    info->head_select = h->head_select;
     info->n_bins = h->n_bins;
     info->obs_tile = h->obs_tile;
     info->warps_per_cta = h->warps_per_cta;
-    info->n_deep_records = h->n_deep;
+    info->n_super = h->n_super;
+    info->n_internal = h->n_internal;
     info->head_bytes = h->head_bytes_total;
-    info->deep_bytes = 8 * h->n_deep;
+    info->deep_bytes = (int64_t)sizeof(FpSuper) * h->n_super;
     info->total_bytes = h->class_bytes;
     info->parity_bytes = h->total_bytes - h->class_bytes;
     info->max_head_bytes = h->max_head_bytes;
     info->passes = h->n_passes;
+    info->refill_lanes = h->refill_lanes;
 }
 
 extern "C" const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes) {

@@ -1,55 +1,66 @@
 // fp_traverse.cuh -- the packed-forest traversal kernel (sm_103a).
 //
 // One work item = (pass, observation tile).  Items are ordered pass-major, so
-// at any moment the whole GPU walks the bins of one pass, whose records stay
-// resident in L2 while every tile of observations goes through them (the
-// GPU counterpart of the paper's bins bound to cores, Section III and
-// Section IV-D).  Within an item the CTA:
-//   1. stages the tile's rows into shared memory with 4-byte cp.async, at an
-//      odd row stride so that lanes reading one feature of 32 rows hit 32
-//      banks;
-//   2. for each bin of the pass, stages the bin's interleaved block (levels
-//      0..d of all its trees plus the link row, Section III-A Bin) into shared
-//      memory with 16-byte cp.async;
-//   3. walks (observation, tree) tasks: the lanes of a warp take consecutive
-//      observations of the same tree, walk the interleaved levels in shared
-//      memory, then the tree's Stat region in global memory, where the hot
-//      child is the next record (Section III-A Stat).  A lane that reaches a
-//      leaf takes the warp's next task at once: free lanes are found with
-//      __ballot_sync and numbered with __popc, so lanes stay busy while paths
-//      of different depth diverge (the GPU form of Section III-B's
-//      round-robin over a bin's trees);
+// at any moment the GPU walks the bins of one pass, whose super-nodes stay
+// resident in L2 while every tile of observations goes through them (the GPU
+// counterpart of the paper's bins bound to cores, Section III).  For an item
+// the CTA:
+//   1. stages the tile's rows into shared memory with 4-byte cp.async,
+//      feature-major (x[f * R + r]), so 32 lanes holding 32 consecutive rows
+//      read any features from 32 different banks;
+//   2. streams the bins' interleaved blocks (the heads of their trees,
+//      Section III-A Bin) through FP_NBUF shared-memory buffers with TMA bulk
+//      copies (cp.async.bulk) completing on mbarriers: a warp waits only for
+//      the block of the bin it is about to claim, and the last warp to finish
+//      claiming a bin refills that buffer with the bin FP_NBUF places ahead;
+//   3. walks (observation, tree) tasks in two kinds of warp steps:
+//        burst -- the warp claims 32 consecutive tasks (32 rows of one tree)
+//                 and all lanes walk their paths through the tree's head in
+//                 shared memory together, with a branch-free step; paths that
+//                 leave the head are pushed, compacted with __ballot_sync /
+//                 __popc, into the warp's ring of pending tasks;
+//        deep  -- every lane holding a task resolves two more levels with one
+//                 32-byte super-node load (one L2 sector); a lane that reaches
+//                 a leaf votes and takes the next pending task from the ring.
+//      Bursts keep the ring topped up, so lanes stay busy while paths of very
+//      different depth diverge -- the GPU form of the paper's round-robin over
+//      independent tasks (Section III-B).  Pending and running tasks carry
+//      over from one bin to the next, and nothing but the item's end makes a
+//      warp wait for another;
 //   4. counts votes per (row, class) with shared-memory atomics;
 //   5. writes votes and the argmax class (lowest class on ties).  With one
-//      pass the tile's votes are complete in shared memory; with several, the
-//      tile's votes are added to a global accumulator and the CTA that
-//      finishes a tile's last pass (per-tile counter, no waiting) takes the
-//      argmax.
+//      pass the tile's votes are complete in shared memory; with several, they
+//      are added to a global accumulator and the CTA that finishes a tile's
+//      last pass (per-tile counter, no waiting) takes the argmax.
 // Parity mode writes the leaf id reached in every (observation, tree)
 // instead of voting.
 //
-// Every wait in this kernel is a hardware wait (cp.async.wait_all,
-// __syncthreads); there is no spin loop.
+// Waits: cp.async.wait_group and __syncthreads are hardware waits; the
+// mbarrier waits poll at most FP_SPIN_LIMIT times, then record FP_ETIMEOUT in
+// the status word and make every warp skip the rest of its work (and wait,
+// again bounded, for the CTA's own bulk copies before exiting).  Every walk is
+// bounded too.
 #pragma once
 #include <stdint.h>
 
 #include "fp_internal.h"
 
 struct TravParams {
-    const uint2 *deep;        // deep records
-    const uint8_t *heads;     // heads section
+    const FpSuper *deep;      // super-nodes
+    const uint8_t *heads;     // interleaved blocks
     const FpBin *bins;
     const FpPass *passes;
     const uint32_t *tree_base;
-    const int32_t *pheads;    // parity heads section
-    const int2 *deep_leaf;    // parity: leaf ids per deep record
+    const int32_t *pheads;    // parity: leaf id per block exit
+    const int32_t *deep_leaf; // parity: 4 leaf ids per super-node
     const float *X;
     int64_t n;
     int64_t n_tiles;
     int64_t n_items;
-    int32_t F, P, C, T, S, Lk, R;
+    int32_t F, C, T, R;
     int32_t n_passes;
     int32_t head_smem;        // bytes reserved for one bin block
+    int32_t refill;           // bursts start when the ring holds at most this many tasks
     uint32_t *out_votes;      // single pass: final votes (may be NULL)
     int32_t *out_class;       // may be NULL
     int32_t *out_leaf;        // parity mode
@@ -58,8 +69,12 @@ struct TravParams {
     int32_t *status;          // device status word
 };
 
-#define FP_STATUS_BAD_CLASS 2
 #define FP_ERR_FLAG_DEVICE (-6)
+#define FP_ERR_FLAG_TIMEOUT (-5)
+#define FP_NBUF 3             // bin-block buffers in flight
+#define FP_SPIN_LIMIT (1 << 24)
+#define FP_RING 64            // pending tasks per warp
+#define FP_NO_CLASS (FP_REF_LEAF | 0x7FFFFFFFu)
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -71,171 +86,293 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ uint2 ld_record(const uint2 *p) {
-    uint2 v;
-    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
+// One super-node: a single 256-bit load (32-byte aligned, one L2 sector).
+__device__ __forceinline__ void ld_super(const FpSuper *p, uint32_t w[8]) {
+    asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
 }
 
 __device__ __forceinline__ void report(int32_t *status, int32_t code) { atomicCAS(status, 0, code); }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// true once the phase of the given parity has completed
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// One thread: copy a bin's block into a buffer with the bulk-copy engine.
+__device__ __forceinline__ void stage_block_bulk(const TravParams &p, int b, uint8_t *dst, uint64_t *bar) {
+    const FpBin bn = p.bins[b];
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of dst come first
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bn.head_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(p.heads + bn.head_off), "r"(bn.head_bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Per-lane state of a running task.
+struct LaneTask {
+    bool active;
+    int r;            // row within the tile
+    int t;            // tree
+    uint32_t ref;     // current super-node (tree-local)
+    uint32_t steps;
+    const FpSuper *tb;
+};
+
+// A finished task: vote, or record the leaf id in parity mode.
 template <bool LEAVES>
-__global__ void __launch_bounds__(1024) fp_traverse_kernel(const TravParams p) {
+__device__ __forceinline__ void finish(const TravParams &p, uint32_t *svotes, int64_t row0, int r, int t,
+                                       uint32_t cls, int32_t leaf_id) {
+    if (LEAVES) {
+        p.out_leaf[(row0 + r) * p.T + t] = leaf_id;
+    } else if (cls < (uint32_t)p.C) {
+        atomicAdd(&svotes[r * p.C + cls], 1u);
+    } else {
+        report(p.status, FP_ERR_FLAG_DEVICE);
+    }
+}
+
+// Lanes without a task take pending ones from the warp's ring.
+__device__ __forceinline__ void pop_tasks(const TravParams &p, const uint2 *ring, int &head, int tail, LaneTask &L,
+                                          unsigned lt_mask) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !L.active);
+    const int npop = min(__popc(idle), tail - head);
+    if (npop <= 0) return;
+    const int rk = __popc(idle & lt_mask);
+    if (!L.active && rk < npop) {
+        const uint2 ent = ring[(head + rk) & (FP_RING - 1)];
+        L.ref = ent.x;
+        L.r = (int)(ent.y & 2047u);
+        L.t = (int)(ent.y >> 11);
+        L.tb = p.deep + p.tree_base[L.t];
+        L.steps = 0;
+        L.active = true;
+    }
+    head += npop;
+}
+
+// One deep step: two levels of the tree per 32-byte load.
+template <bool LEAVES>
+__device__ __forceinline__ void deep_step(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
+                                          LaneTask &L) {
+    uint32_t w[8];
+    ld_super(L.tb + L.ref, w);
+    const int R = p.R;
+    const float x0 = xs[(w[3] & 1023u) * R + L.r];
+    const uint32_t d0 = x0 <= __uint_as_float(w[0]) ? 0u : 1u;
+    const uint32_t f1 = d0 ? (w[3] >> 20) & 1023u : (w[3] >> 10) & 1023u;
+    const uint32_t t1 = d0 ? w[2] : w[1];
+    const float x1 = xs[f1 * R + L.r];
+    const uint32_t d1 = x1 <= __uint_as_float(t1) ? 0u : 1u;
+    const uint32_t nref = d0 ? (d1 ? w[7] : w[6]) : (d1 ? w[5] : w[4]);
+    if (nref & FP_REF_LEAF) {
+        L.active = false;
+        int32_t leaf_id = -1;
+        if (LEAVES) leaf_id = p.deep_leaf[4 * ((int64_t)(L.tb - p.deep) + L.ref) + 2 * d0 + d1];
+        finish<LEAVES>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
+    } else if (++L.steps < (1u << 24)) {  // a path is shorter than any tree
+        L.ref = nref;
+    } else {
+        report(p.status, FP_ERR_FLAG_DEVICE);
+        L.active = false;
+    }
+}
+
+template <bool LEAVES>
+__global__ void __launch_bounds__(1024, 1) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_task_next;
+    __shared__ __align__(8) uint64_t s_full[FP_NBUF];  // block staged (bulk copy done)
+    __shared__ int s_task_next[FP_NBUF];               // next unclaimed task of the buffer's bin
+    __shared__ int s_claim_done[FP_NBUF];              // warps done claiming the buffer's bin
+    __shared__ int s_issued[FP_NBUF];                  // bulk copies issued into the buffer
     __shared__ int s_last;
-    const int R = p.R, P = p.P, F = p.F, C = p.C, S = p.S;
+    __shared__ int s_abort;
+    const int R = p.R, F = p.F, C = p.C;
     float *xs = reinterpret_cast<float *>(smem);
-    const int xs_bytes = ((R * P * 4) + 15) & ~15;
-    uint8_t *hbuf = smem + xs_bytes;
-    uint32_t *svotes = reinterpret_cast<uint32_t *>(hbuf + p.head_smem);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int xs_bytes = ((F * R * 4) + 15) & ~15;
+    uint8_t *const hbuf0 = smem + xs_bytes;  // FP_NBUF bin-block buffers, head_smem bytes each
+    uint32_t *svotes = reinterpret_cast<uint32_t *>(smem + xs_bytes + FP_NBUF * p.head_smem);
+    const int vote_bytes = LEAVES ? 0 : ((R * C * 4) + 15) & ~15;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    uint2 *ring = reinterpret_cast<uint2 *>(smem + xs_bytes + FP_NBUF * p.head_smem + vote_bytes) + warp * FP_RING;
     const unsigned lt_mask = (1u << lane) - 1u;
+
+    if (tid == 0) {
+        for (int i = 0; i < FP_NBUF; ++i) {
+            mbar_init(&s_full[i], 1);
+            s_issued[i] = 0;
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t seq_base = 0;  // bins this CTA has staged before the current item
+
+    // one thread: stage bin b as the CTA's seq-th bin
+    auto issue = [&](int b, uint32_t seq) {
+        const int buf = (int)(seq % FP_NBUF);
+        s_task_next[buf] = 0;
+        s_claim_done[buf] = 0;
+        s_issued[buf] += 1;
+        stage_block_bulk(p, b, hbuf0 + buf * p.head_smem, &s_full[buf]);
+    };
 
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const int pass = (int)(item / p.n_tiles);
         const int64_t tile = item - (int64_t)pass * p.n_tiles;
         const int64_t row0 = tile * R;
         const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
+        const FpPass ps = p.passes[pass];
+        const int nbins = ps.bin_end - ps.bin_begin;
 
-        // 1. rows -> shared memory (odd stride P)
+        // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
         {
             const float *src = p.X + row0 * F;
             const int total = rows * F;
             for (int e = tid; e < total; e += blockDim.x) {
                 const int r = e / F;
-                cp_async4(xs + r * P + (e - r * F), src + e);
+                cp_async4(xs + (e - r * F) * R + r, src + e);
             }
+            cp_async_commit();
         }
+        if (tid == 0 && !s_abort)
+            for (int i = 0; i < FP_NBUF && i < nbins; ++i) issue(ps.bin_begin + i, seq_base + i);
         if (!LEAVES)
             for (int i = tid; i < rows * C; i += blockDim.x) svotes[i] = 0;
+        cp_async_wait_all();
+        __syncthreads();
 
-        const FpPass ps = p.passes[pass];
-        for (int b = ps.bin_begin; b < ps.bin_end; ++b) {
+        LaneTask L;
+        L.active = false;
+        L.r = 0;
+        L.t = 0;
+        L.ref = 0;
+        L.steps = 0;
+        L.tb = p.deep;
+        int head = 0, tail = 0;  // warp-uniform ring cursors
+
+        for (int bi = 0; bi < nbins; ++bi) {
+            const uint32_t seq = seq_base + bi;
+            const int buf = (int)(seq % FP_NBUF);
+            {  // wait until the bin's block has landed
+                const uint32_t parity = (seq / FP_NBUF) & 1u;
+                bool ok = false;
+                for (int spin = 0; spin < FP_SPIN_LIMIT; ++spin) {
+                    if (*(volatile int *)&s_abort) break;
+                    if (mbar_try_wait(&s_full[buf], parity)) {
+                        ok = true;
+                        break;
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0 && !*(volatile int *)&s_abort) {
+                        report(p.status, FP_ERR_FLAG_TIMEOUT);
+                        *(volatile int *)&s_abort = 1;
+                    }
+                    break;
+                }
+            }
+            const int b = ps.bin_begin + bi;
             const FpBin bn = p.bins[b];
-            // 2. interleaved block -> shared memory
-            {
-                const uint8_t *src = p.heads + bn.head_off;
-                for (int o = tid * 16; o < (int)bn.head_bytes; o += blockDim.x * 16) cp_async16(hbuf + o, src + o);
-            }
-            if (tid == 0) s_task_next = 0;
-            cp_async_wait_all();
-            __syncthreads();
+            const int stride = bn.stride, nranks = bn.nranks, nexits = bn.nexits;
+            const int ntask = rows * bn.width;
+            const uint8_t *blk = hbuf0 + buf * p.head_smem;
+            const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
+            const uint32_t *hexit = reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * 8);
+            volatile int *next = &s_task_next[buf];
 
-            // 3. walk (observation, tree) tasks
-            const int width = bn.width;
-            const int ntask = rows * width;
-            const uint2 *hrec = reinterpret_cast<const uint2 *>(hbuf);
-            const uint32_t *hlink = reinterpret_cast<const uint32_t *>(hbuf + (size_t)S * width * 8);
-            int pool_next = 0, pool_end = 0;  // warp-uniform local task window
-            bool exhausted = false;           // warp-uniform: the bin's tasks are all claimed
-            bool active = false;
-            int r = 0, k = 0;
-            uint32_t idx = 0;
-            const uint2 *tdeep = p.deep;
-            const float *xrow = xs;
             for (;;) {
-                // refill free lanes; a new task first walks the interleaved levels
-                while (!exhausted) {
-                    const unsigned free_mask = __ballot_sync(0xffffffffu, !active);
-                    if (free_mask == 0) break;
-                    if (pool_next >= pool_end) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&s_task_next, 32);
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (base >= ntask) {
-                            exhausted = true;
-                            break;
-                        }
-                        pool_next = base;
-                        pool_end = min(base + 32, ntask);
-                    }
-                    const int avail = pool_end - pool_next;
-                    const int rank = __popc(free_mask & lt_mask);
-                    const bool take = !active && rank < avail;
-                    const int task = pool_next + rank;
-                    pool_next += min(avail, __popc(free_mask));
-                    if (!take) continue;
-                    k = task / rows;
-                    r = task - k * rows;
-                    xrow = xs + r * P;
-                    const int t = bn.first_tree + k;
-                    // interleaved levels 0..d
-                    int s = 0;
-                    int32_t cls = -1, leaf_id = -1;
-                    bool done = false;
-                    for (;;) {
-                        const uint2 rec = hrec[s * width + k];
-                        if (rec.y & FP_HEAD_LEAF) {
-                            cls = (int32_t)(rec.y & 0x7FFFFFFFu);
-                            if (LEAVES) leaf_id = p.pheads[(bn.phead_off >> 2) + s * width + k];
-                            done = true;
-                            break;
-                        }
-                        const float x = xrow[rec.y];
-                        s = 2 * s + 1 + (x <= __uint_as_float(rec.x) ? 0 : 1);
-                        if (s >= S) {
-                            const uint32_t e = hlink[(s - S) * width + k];
-                            if (e & FP_HEAD_LEAF) {
-                                cls = (int32_t)(e & 0x7FFFFFFFu);
-                                if (LEAVES) leaf_id = p.pheads[(bn.phead_off >> 2) + s * width + k];
-                                done = true;
-                            } else {
-                                idx = e;
-                                tdeep = p.deep + p.tree_base[t];
-                                active = true;
+                if (*next >= ntask) break;  // the bin's tasks are all claimed
+                if (tail - head <= p.refill) {
+                    // burst: 32 consecutive tasks through the head, all lanes together
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_task_next[buf], 32);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (base >= ntask) break;
+                    const bool my = lane < ntask - base;
+                    const int task = base + lane;
+                    const int k2 = my ? task / rows : 0;
+                    const int r2 = my ? task - k2 * rows : 0;
+                    uint32_t hr = 0;  // head rank, then nranks + exit index
+                    bool busy = my;
+                    int guard = 0;
+                    while (__any_sync(0xffffffffu, busy)) {
+                        if (busy) {
+                            const uint2 nd = hnode[hr * stride + k2];
+                            const uint32_t m = nd.y;
+                            hr = xs[(m >> 22) * R + r2] <= __uint_as_float(nd.x) ? (m & FP_TARGET_MASK)
+                                                                                   : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
+                            busy = hr < (uint32_t)nranks;
+                            if (++guard > nranks && busy) {  // a path visits each rank at most once
+                                report(p.status, FP_ERR_FLAG_DEVICE);
+                                busy = false;
+                                hr = (uint32_t)(nranks + nexits);
                             }
-                            break;
                         }
                     }
-                    if (done) {
-                        if (LEAVES) {
-                            p.out_leaf[(row0 + r) * p.T + t] = leaf_id;
-                        } else if ((unsigned)cls < (unsigned)C) {
-                            atomicAdd(&svotes[r * C + cls], 1u);
-                        } else {
-                            report(p.status, FP_ERR_FLAG_DEVICE);
-                        }
+                    const uint32_t e = hr - (uint32_t)nranks;
+                    const uint32_t er = (my && e < (uint32_t)nexits) ? hexit[e * stride + k2] : FP_NO_CLASS;
+                    const int t2 = bn.first_tree + k2;
+                    if (my && (er & FP_REF_LEAF)) {
+                        int32_t leaf_id = -1;
+                        if (LEAVES && e < (uint32_t)nexits) leaf_id = p.pheads[(bn.phead_off >> 2) + e * stride + k2];
+                        finish<LEAVES>(p, svotes, row0, r2, t2, er & 0x7FFFFFFFu, leaf_id);
                     }
+                    const bool push = my && !(er & FP_REF_LEAF);
+                    const unsigned pm = __ballot_sync(0xffffffffu, push);
+                    if (push)
+                        ring[(tail + __popc(pm & lt_mask)) & (FP_RING - 1)] =
+                            make_uint2(er, (uint32_t)r2 | ((uint32_t)t2 << 11));
+                    tail += __popc(pm);
+                    __syncwarp();
                 }
-                if (__ballot_sync(0xffffffffu, active) == 0) break;
-                // one level of the Stat region for every active lane
-                if (active) {
-                    const uint2 rec = ld_record(tdeep + idx);
-                    const uint32_t m = rec.y;
-                    const float x = xrow[m >> FP_META_FEATURE_SHIFT];
-                    const uint32_t right = x <= __uint_as_float(rec.x) ? 0u : 1u;
-                    const uint32_t pay = m & FP_META_PAYLOAD_MASK;
-                    int32_t cls = -1;
-                    if (m & FP_META_BOTH_LEAF) {
-                        cls = (int32_t)(right ? (pay >> 9) : (pay & 511u));
-                    } else if (right == ((m >> 21) & 1u)) {
-                        idx += 1;
-                    } else if (m & FP_META_COLD_LEAF) {
-                        cls = (int32_t)pay;
-                    } else {
-                        idx = pay;
-                    }
-                    if (cls >= 0) {
-                        active = false;
-                        if (LEAVES) {
-                            const int2 lf = p.deep_leaf[(tdeep - p.deep) + idx];
-                            p.out_leaf[(row0 + r) * p.T + bn.first_tree + k] = right ? lf.y : lf.x;
-                        } else if (cls < C) {
-                            atomicAdd(&svotes[r * C + cls], 1u);
-                        } else {
-                            report(p.status, FP_ERR_FLAG_DEVICE);
-                        }
-                    }
-                }
+                pop_tasks(p, ring, head, tail, L, lt_mask);
+                if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
             }
-            __syncthreads();  // the next bin overwrites the block
+            // this warp reads the bin's block no more; the last warp refills the buffer
+            __syncwarp();
+            if (lane == 0) {
+                const int done = atomicAdd(&s_claim_done[buf], 1);
+                if (done == nwarps - 1 && bi + FP_NBUF < nbins && !*(volatile int *)&s_abort)
+                    issue(ps.bin_begin + bi + FP_NBUF, seq + FP_NBUF);
+            }
+            __syncwarp();
         }
+        seq_base += (uint32_t)nbins;
+        const bool aborted = *(volatile int *)&s_abort != 0;
+        // drain: the item's last pending and running tasks
+        for (; !aborted;) {
+            __syncwarp();
+            pop_tasks(p, ring, head, tail, L, lt_mask);
+            if (!__any_sync(0xffffffffu, L.active)) break;
+            if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
+        }
+        __syncthreads();
 
         // 5. votes and class
-        if (!LEAVES) {
+        if (!LEAVES && !*(volatile int *)&s_abort) {
             if (p.n_passes == 1) {
                 if (p.out_votes) {
                     uint32_t *dst = p.out_votes + row0 * C;
@@ -279,5 +416,14 @@ __global__ void __launch_bounds__(1024) fp_traverse_kernel(const TravParams p) {
             }
         }
         __syncthreads();  // the next item reuses shared memory
+    }
+    // after an abort, let this CTA's bulk copies land before it exits (bounded)
+    if (tid == 0 && s_abort) {
+        for (int i = 0; i < FP_NBUF; ++i) {
+            if (s_issued[i] == 0) continue;
+            const uint32_t parity = (uint32_t)(s_issued[i] - 1) & 1u;
+            for (int spin = 0; spin < FP_SPIN_LIMIT && !mbar_try_wait(&s_full[i], parity); ++spin) {
+            }
+        }
     }
 }

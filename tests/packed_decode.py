@@ -7,20 +7,17 @@ import numpy as np
 
 HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_trees", "<i4"), ("n_features", "<i4"),
                 ("n_classes", "<i4"), ("bin_size", "<i4"), ("depth", "<i4"), ("n_bins", "<i4"),
-                ("n_passes", "<i4"), ("slots", "<i4"), ("links", "<i4"), ("obs_tile", "<i4"),
-                ("warps_per_cta", "<i4"), ("max_head_bytes", "<i4"), ("n_deep", "<i8"), ("off_bins", "<i8"),
-                ("off_passes", "<i8"), ("off_tree_base", "<i8"), ("off_heads", "<i8"), ("off_deep", "<i8"),
-                ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"), ("total_bytes", "<i8"),
-                ("head_bytes_total", "<i8"), ("pass_bytes", "<i8")], align=True)
+                ("n_passes", "<i4"), ("head_nodes", "<i4"), ("head_select", "<i4"), ("obs_tile", "<i4"),
+                ("warps_per_cta", "<i4"), ("max_head_bytes", "<i4"), ("refill_lanes", "<i4"), ("n_super", "<i8"),
+                ("off_bins", "<i8"), ("off_passes", "<i8"), ("off_tree_base", "<i8"), ("off_heads", "<i8"),
+                ("off_deep", "<i8"), ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"),
+                ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8")],
+               align=True)
 BIN = np.dtype([("head_off", "<u4"), ("head_bytes", "<u4"), ("first_tree", "<i4"), ("width", "<i4"),
-                ("phead_off", "<u4"), ("pad", "<u4", 3)])
+                ("phead_off", "<u4"), ("stride", "<i4"), ("nranks", "<i4"), ("nexits", "<i4")])
 PASS = np.dtype([("bin_begin", "<i4"), ("bin_end", "<i4")])
 
 LEAF = 0x80000000
-HOT_RIGHT = 1 << 21
-COLD_LEAF = 1 << 20
-BOTH_LEAF = 1 << 19
-PAYLOAD = 0x7FFFF
 
 
 class Image:
@@ -32,78 +29,71 @@ class Image:
         self.bins = np.frombuffer(img[g["off_bins"]: g["off_bins"] + BIN.itemsize * g["n_bins"]].tobytes(), BIN)
         self.passes = np.frombuffer(img[g["off_passes"]: g["off_passes"] + 8 * g["n_passes"]].tobytes(), PASS)
         self.tree_base = img[g["off_tree_base"]: g["off_tree_base"] + 4 * g["n_trees"]].view("<u4")
-        deep = img[g["off_deep"]: g["off_deep"] + 8 * g["n_deep"]]
-        self.deep_thr = deep.view("<f4")[0::2]
-        self.deep_meta = deep.view("<u4")[1::2]
-        dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 8 * g["n_deep"]].view("<i4")
-        self.deep_leaf = dl.reshape(-1, 2)
+        deep = img[g["off_deep"]: g["off_deep"] + 32 * g["n_super"]]
+        self.sw = deep.view("<u4").reshape(-1, 8)          # super-node words
+        self.sthr = deep.view("<f4").reshape(-1, 8)[:, :3]  # thresholds of v, left, right
+        dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 16 * g["n_super"]].view("<i4")
+        self.deep_leaf = dl.reshape(-1, 4)
 
     def head(self, b: int):
-        """(thr [S][w], meta [S][w], link [L][w], parity [S+L][w]) of bin b."""
+        """(thr [nranks][stride], meta [nranks][stride], exits [nexits][stride],
+        exit leaf ids [nexits][stride]) of bin b's interleaved block."""
         g, bn = self.h, self.bins[b]
-        w, S, L = int(bn["width"]), g["slots"], g["links"]
+        st, nr, ne = int(bn["stride"]), int(bn["nranks"]), int(bn["nexits"])
         base = g["off_heads"] + int(bn["head_off"])
-        recs = self.img[base: base + 8 * S * w]
-        thr = recs.view("<f4")[0::2].reshape(S, w)
-        meta = recs.view("<u4")[1::2].reshape(S, w)
-        link = self.img[base + 8 * S * w: base + 8 * S * w + 4 * L * w].view("<u4").reshape(L, w)
+        recs = self.img[base: base + 8 * nr * st]
+        thr = recs.view("<f4")[0::2].reshape(nr, st)
+        meta = recs.view("<u4")[1::2].reshape(nr, st)
+        exits = self.img[base + 8 * nr * st: base + 8 * nr * st + 4 * ne * st].view("<u4").reshape(ne, st)
         pb = g["off_pheads"] + int(bn["phead_off"])
-        par = self.img[pb: pb + 4 * (S + L) * w].view("<i4").reshape(S + L, w)
-        return thr, meta, link, par
+        par = self.img[pb: pb + 4 * ne * st].view("<i4").reshape(ne, st)
+        return thr, meta, exits, par
 
     def walk(self, X: np.ndarray):
         """Leaf id and class per (observation, tree), decoding the records."""
         g = self.h
-        n, T, S = X.shape[0], g["n_trees"], g["slots"]
+        n, T = X.shape[0], g["n_trees"]
         leaf = np.full((n, T), -2, np.int32)
         cls = np.full((n, T), -2, np.int32)
         rows = np.arange(n)
         for b in range(g["n_bins"]):
-            thr, meta, link, par = self.head(b)
+            thr, meta, exits, par = self.head(b)
             bn = self.bins[b]
             for k in range(int(bn["width"])):
                 t = int(bn["first_tree"]) + k
-                s = np.zeros(n, np.int64)
-                idx = np.full(n, -1, np.int64)
-                state = np.zeros(n, np.int8)  # 0 head, 1 deep, 2 done
-                while np.any(state == 0):
-                    a = rows[state == 0]
-                    m = meta[s[a], k]
-                    is_leaf = (m & LEAF) != 0
-                    la = a[is_leaf]
-                    cls[la, t] = (m[is_leaf] & 0x7FFFFFFF).astype(np.int32)
-                    leaf[la, t] = par[s[la], k]
-                    state[la] = 2
-                    a, m = a[~is_leaf], m[~is_leaf]
-                    x = X[a, m.astype(np.int64)]
-                    right = ~(x <= thr[s[a], k])
-                    s[a] = 2 * s[a] + 1 + right
-                    out = a[s[a] >= S]
-                    e = link[s[out] - S, k]
-                    el = (e & LEAF) != 0
-                    cls[out[el], t] = (e[el] & 0x7FFFFFFF).astype(np.int32)
-                    leaf[out[el], t] = par[s[out[el]], k]
-                    state[out[el]] = 2
-                    idx[out[~el]] = e[~el]
-                    state[out[~el]] = 1
+                nr = int(bn["nranks"])
+                hr = np.zeros(n, np.int64)
+                busy = np.ones(n, bool)
+                while np.any(busy):
+                    a = rows[busy]
+                    m = meta[hr[a], k].astype(np.int64)
+                    right = ~(X[a, m >> 22] <= thr[hr[a], k])
+                    hr[a] = np.where(right, (m >> 11) & 2047, m & 2047)
+                    busy[a] = hr[a] < nr
+                e = hr - nr
+                ref = exits[e, k]
+                lf = (ref & LEAF) != 0
+                cls[lf, t] = (ref[lf] & 0x7FFFFFFF).astype(np.int32)
+                leaf[lf, t] = par[e[lf], k]
+                state = np.where(lf, 2, 1).astype(np.int8)
+                idx = np.where(lf, -1, ref.astype(np.int64))
                 base = int(self.tree_base[t])
                 while np.any(state == 1):
                     a = rows[state == 1]
                     g_idx = base + idx[a]
-                    m = self.deep_meta[g_idx]
-                    x = X[a, (m >> 22).astype(np.int64)]
-                    right = ~(x <= self.deep_thr[g_idx])
-                    pay = m & PAYLOAD
-                    both = (m & BOTH_LEAF) != 0
-                    hot = (right.astype(np.uint32) == ((m >> 21) & 1)) & ~both
-                    cold_leaf = (m & COLD_LEAF) != 0
-                    fin = both | (~hot & cold_leaf)
-                    c = np.where(both, np.where(right, pay >> 9, pay & 511), pay)
+                    w = self.sw[g_idx]
+                    th = self.sthr[g_idx]
+                    f0 = (w[:, 3] & 1023).astype(np.int64)
+                    d0 = ~(X[a, f0] <= th[:, 0])
+                    f1 = np.where(d0, (w[:, 3] >> 20) & 1023, (w[:, 3] >> 10) & 1023).astype(np.int64)
+                    t1 = np.where(d0, th[:, 2], th[:, 1])
+                    d1 = ~(X[a, f1] <= t1)
+                    slot = 2 * d0.astype(np.int64) + d1.astype(np.int64)
+                    nref = w[np.arange(len(a)), 4 + slot]
+                    fin = (nref & LEAF) != 0
                     fa = a[fin]
-                    cls[fa, t] = c[fin].astype(np.int32)
-                    leaf[fa, t] = self.deep_leaf[g_idx[fin], right[fin].astype(np.int64)]
+                    cls[fa, t] = (nref[fin] & 0x7FFFFFFF).astype(np.int32)
+                    leaf[fa, t] = self.deep_leaf[g_idx[fin], slot[fin]]
                     state[fa] = 2
-                    idx[a[hot]] += 1
-                    jump = ~fin & ~hot
-                    idx[a[jump]] = pay[jump]
+                    idx[a[~fin]] = nref[~fin]
         return leaf, cls

@@ -1,0 +1,60 @@
+"""Full-size parity at the launch configuration bench.py times.
+
+The HBM-resident workload (256 trees, 4,000,000 rows) and the image-shaped
+workload (128 trees, 1,000,000 rows) run exactly as the benchmark runs them.
+Every row is checked against properties that hold at any size (votes sum to
+the tree count; the class is the first maximal vote); a seeded sample of rows
+is checked element by element against the oracle, votes, classes and per-tree
+leaf ids."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_1806_07300_gb300 as fp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SAMPLE = 20000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _run(name, n):
+    forest = datagen.forest(name)
+    X, _ = datagen.test_rows(name, n)
+    df = fp.fp_upload(fp.fp_pack_forest(forest))  # the benchmark's default parameters
+    Xd = torch.from_numpy(X).cuda()
+    votes, cls = df.predict(Xd)
+    torch.cuda.synchronize()
+    assert df.sync_status() == fp.FP_OK
+    v = votes.cpu().numpy().astype(np.uint32)
+    c = cls.cpu().numpy()
+    # properties of every row
+    assert np.all(v.sum(axis=1) == forest.n_trees)
+    np.testing.assert_array_equal(c, np.argmax(v, axis=1))
+    # seeded sample, element by element
+    rng = np.random.Generator(np.random.PCG64(1234))
+    idx = np.sort(rng.choice(n, size=min(SAMPLE, n), replace=False))
+    idx[-1] = n - 1  # include the ragged last tile
+    ref = oracle.predict(forest, X[idx], threads=oracle.default_threads())
+    np.testing.assert_array_equal(v[idx], ref["votes"])
+    np.testing.assert_array_equal(c[idx], ref["cls"])
+    leaves = df.predict_leaves(torch.from_numpy(np.ascontiguousarray(X[idx])).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
+    df.release()
+
+
+def test_hbm_workload_full_size():
+    _run("hbm", datagen.RECIPES["hbm"]["n_test"])
+
+
+def test_image_workload_full_size():
+    _run("image", datagen.RECIPES["image"]["n_test"])

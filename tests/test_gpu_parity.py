@@ -58,7 +58,7 @@ def test_hand_fixtures_on_gpu(name, B, d):
     _check_all(forest, X, ref, bin_size=B, interleave_depth=d)
 
 
-@pytest.mark.parametrize("B,d", [(16, 4), (1, 0), (5, 2), (7, 6), (16, 9)])
+@pytest.mark.parametrize("B,d", [(16, 4), (1, 0), (5, 2), (7, 6), (4, 9)])
 def test_tiny_workload(tiny_forest, tiny_rows, B, d):
     X, _ = tiny_rows
     _check_all(tiny_forest, X, bin_size=B, interleave_depth=d)
@@ -70,7 +70,7 @@ def test_tiny_tiles_and_ragged_tail(tiny_forest, tiny_rows, tile, warps):
     _check_all(tiny_forest, X[:tile * 3 + 17], bin_size=4, interleave_depth=2, obs_tile=tile, warps_per_cta=warps)
 
 
-@pytest.mark.parametrize("pass_bytes", [1, 4096, 65536])
+@pytest.mark.parametrize("pass_bytes", [1, 2048, 8192])
 def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes):
     """Several passes: global accumulation and last-pass argmax."""
     X, _ = tiny_rows
@@ -151,5 +151,5 @@ def test_image_workload_params_grid():
     forest = datagen.forest("image")
     X, _ = datagen.test_rows("image", 3000)
     ref = oracle.predict(forest, X, threads=oracle.default_threads())
-    for B, d in [(128, 1), (16, 3), (32, 6)]:
+    for B, d in [(128, 1), (16, 3), (8, 5), (1, 9)]:
         _check_all(forest, X, ref, bin_size=B, interleave_depth=d)

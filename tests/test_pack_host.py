@@ -12,7 +12,7 @@ import datagen
 import oracle
 import paper_1806_07300_gb300 as fp
 from golden_io import load
-from packed_decode import Image, HOT_RIGHT, BOTH_LEAF, COLD_LEAF, PAYLOAD
+from packed_decode import Image, LEAF
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -57,55 +57,149 @@ def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d):
     np.testing.assert_array_equal(cls, tiny_forest.leaf_class[tiny_forest.node_begin[:-1][None, :] + ref["leaf"]])
 
 
-def test_stat_order_in_packed_records(tiny_forest):
-    """Below the interleaved levels the hot child sits right after its parent
-    (Section III-A, Stat): the record at index+1 is the hot child's."""
+def _head_nodes(forest, t, im):
+    """Node ids of tree t's head, in rank order, recovered by walking the block."""
+    B = im.h["bin_size"]
+    b, k = t // B, t % B
+    thr, meta, exits, par = im.head(b)
+    tr = forest.tree(t)
+    if tr["left"][0] < 0:
+        return [], {}
+    rank_node = {0: 0}
+    exit_node = {}
+    nr = int(im.bins[b]["nranks"])
+    for r in range(meta.shape[0]):
+        if r not in rank_node:
+            continue
+        v = rank_node[r]
+        m = int(meta[r, k])
+        assert m >> 22 == tr["feature"][v] and thr[r, k] == tr["threshold"][v]
+        for c, tgt in ((int(tr["left"][v]), m & 2047), (int(tr["right"][v]), (m >> 11) & 2047)):
+            if tgt < nr:
+                assert tr["left"][c] >= 0, "a head target is an internal node"
+                rank_node[tgt] = c
+            else:
+                exit_node[tgt - nr] = c
+    ranks = sorted(rank_node)
+    assert ranks == list(range(len(ranks))), "head ranks are dense"
+    return [rank_node[r] for r in ranks], exit_node
+
+
+def _super_roots(forest, t, im, exit_node):
+    b, k = t // im.h["bin_size"], t % im.h["bin_size"]
+    _, _, exits, _ = im.head(b)
+    base = int(im.tree_base[t])
+    tr = forest.tree(t)
+    roots = {}
+    stack = [(int(exits[e, k]), v) for e, v in exit_node.items() if not int(exits[e, k]) & LEAF]
+    while stack:
+        i, v = stack.pop()
+        roots[i] = v
+        l, r = int(tr["left"][v]), int(tr["right"][v])
+        ex = [l, l] if tr["left"][l] < 0 else [int(tr["left"][l]), int(tr["right"][l])]
+        ex += [r, r] if tr["left"][r] < 0 else [int(tr["left"][r]), int(tr["right"][r])]
+        for q in range(4):
+            ref = int(im.sw[base + i, 4 + q])
+            if not ref & LEAF:
+                stack.append((ref, ex[q]))
+    return roots
+
+
+@pytest.mark.parametrize("d", [0, 2, 5])
+def test_head_is_top_cardinality_and_stat_ranked(tiny_forest, d):
+    """A tree's head holds its 2^(d+1)-1 internal nodes of highest training
+    cardinality (ties: shallower first), the most popular paths of
+    Section III-A; within the head the first child visited sits at the next
+    rank and is the child of larger cardinality (Stat)."""
     f = tiny_forest
-    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=1)
-    im = Image(pk.image())
-    m = im.deep_meta
+    im = Image(fp.fp_pack_forest(f, bin_size=3, interleave_depth=d).image())
+    K = 2 ** (d + 1) - 1
     for t in range(f.n_trees):
         tr = f.tree(t)
-        a, b = int(im.tree_base[t]), (int(im.tree_base[t + 1]) if t + 1 < f.n_trees else len(m))
-        for i in range(a, b):
-            mm = int(m[i])
-            if mm & BOTH_LEAF:
-                continue
-            hot_right = bool(mm & HOT_RIGHT)
-            assert i + 1 < b
-            nxt = int(m[i + 1])
-            feat = mm >> 22
-            # the hot child record must exist at i+1 and be internal
-            assert (nxt >> 22) < f.n_features
-            if not (mm & COLD_LEAF):
-                assert (mm & PAYLOAD) > i - a, "the cold subtree follows the hot one"
-            del feat, hot_right
+        head, _ = _head_nodes(f, t, im)
+        depth = {0: 0}
+        for v in range(len(tr["left"])):
+            if tr["left"][v] >= 0:
+                depth[int(tr["left"][v])] = depth[v] + 1
+                depth[int(tr["right"][v])] = depth[v] + 1
+        internal = [v for v in range(len(tr["left"])) if tr["left"][v] >= 0]
+        want = sorted(internal, key=lambda v: (-int(tr["cardinality"][v]), depth[v], v))[:K]
+        assert sorted(head) == sorted(want)
+        for i, v in enumerate(head[:-1]):
+            l, r = int(tr["left"][v]), int(tr["right"][v])
+            if head[i + 1] in (l, r):  # depth-first: the first child visited is the more popular one
+                other = r if head[i + 1] == l else l
+                if other in head:
+                    assert tr["cardinality"][head[i + 1]] >= tr["cardinality"][other]
+
+
+def test_head_select_levels(tiny_forest):
+    f = tiny_forest
+    d = 3
+    im = Image(fp.fp_pack_forest(f, bin_size=5, interleave_depth=d, head_select=1).image())
+    for t in range(f.n_trees):
+        tr = f.tree(t)
+        head, _ = _head_nodes(f, t, im)
+        depth = {0: 0}
+        for v in range(len(tr["left"])):
+            if tr["left"][v] >= 0:
+                depth[int(tr["left"][v])] = depth[v] + 1
+                depth[int(tr["right"][v])] = depth[v] + 1
+        want = [v for v in range(len(tr["left"])) if tr["left"][v] >= 0 and depth[v] <= d]
+        assert sorted(head) == sorted(want)
+
+
+def test_stat_order_in_super_nodes(tiny_forest):
+    """Below the head each super-node is followed by its most frequently
+    reached child super-node (Section III-A, Stat), and every internal node
+    lies in the head or in exactly one super-node."""
+    f = tiny_forest
+    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=2)
+    im = Image(pk.image())
+    total = 0
+    for t in range(f.n_trees):
+        tr = f.tree(t)
+        head, exit_node = _head_nodes(f, t, im)
+        roots = _super_roots(f, t, im, exit_node)
+        base = int(im.tree_base[t])
+        n_t = (int(im.tree_base[t + 1]) if t + 1 < f.n_trees else im.sw.shape[0]) - base
+        assert sorted(roots) == list(range(n_t))
+        for i, v in roots.items():
+            kids = sorted({int(im.sw[base + i, 4 + q]) for q in range(4)} - {c for c in
+                          (int(im.sw[base + i, 4 + q]) for q in range(4)) if c & LEAF})
+            if kids:
+                card = {c: int(tr["cardinality"][roots[c]]) for c in kids}
+                assert i + 1 in kids and card[i + 1] == max(card.values()), "hottest child super-node follows"
+        covered = set(head)
+        for v in roots.values():
+            covered.add(v)
+            for c in (int(tr["left"][v]), int(tr["right"][v])):
+                if tr["left"][c] >= 0:
+                    covered.add(c)
+        total += len(covered)
+    assert total == pk.info()["n_internal"]
 
 
 def test_head_interleaving_roots_contiguous(tiny_forest):
-    """Fig. 2 caption: depth 0 puts the roots of a bin's trees side by side."""
+    """Fig. 2 caption: the roots of a bin's trees sit side by side (rank 0),
+    then the trees' next nodes, rank by rank."""
     f = tiny_forest
-    pk = fp.fp_pack_forest(f, bin_size=8, interleave_depth=0)
-    im = Image(pk.image())
+    im = Image(fp.fp_pack_forest(f, bin_size=8, interleave_depth=0).image())
     for b in range(im.h["n_bins"]):
-        thr, meta, link, par = im.head(b)
+        thr, meta, exits, par = im.head(b)
+        assert meta.shape[0] == 1  # d = 0: one node (the root) per tree
         first = int(im.bins[b]["first_tree"])
-        for k in range(meta.shape[1]):
-            t = first + k
-            root = int(f.node_begin[t])
-            assert meta[0, k] == f.feature[root]
+        for k in range(int(im.bins[b]["width"])):
+            root = int(f.node_begin[first + k])
+            assert meta[0, k] >> 22 == f.feature[root]
             assert thr[0, k] == f.threshold[root]
 
 
 def test_pack_info_sizes(tiny_forest):
     pk = fp.fp_pack_forest(tiny_forest, bin_size=16, interleave_depth=2)
     info = pk.info()
-    internal = int((tiny_forest.left >= 0).sum())
-    # nodes at levels 0..2 live in the interleaved block; the rest are records
-    im = Image(pk.image())
-    in_head = sum(int(((im.head(b)[1] & 0x80000000) == 0).sum()) for b in range(im.h["n_bins"]))
-    assert info["n_deep_records"] + in_head == internal
-    assert info["deep_bytes"] == 8 * info["n_deep_records"]
+    assert info["n_internal"] == int((tiny_forest.left >= 0).sum())
+    assert info["deep_bytes"] == 32 * info["n_super"]
     assert info["n_bins"] == 1 and info["passes"] == 1
 
 
@@ -152,7 +246,7 @@ def test_unsupported_sizes_rejected():
     assert ei.value.code == fp.FP_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=12), dict(obs_tile=33),
+@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(obs_tile=33),
                                 dict(warps_per_cta=40)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
