@@ -37,33 +37,32 @@ struct fp_device_forest {
 namespace {
 
 std::mutex g_pool_mu;
-std::vector<cudaMemPool_t> g_pools;
+std::vector<int> g_pool_ready;
 
 int cuda_fail(cudaError_t e, const char *what) {
     fp_set_error("%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ECUDA;
 }
 
-// Library-owned stream-ordered pool for per-call scratch, one per device.
-int scratch_pool(int device, cudaMemPool_t *out) {
-    std::lock_guard<std::mutex> lk(g_pool_mu);
-    if ((int)g_pools.size() <= device) g_pools.resize((size_t)device + 1, nullptr);
-    if (!g_pools[device]) {
-        cudaMemPoolProps props;
-        memset(&props, 0, sizeof props);
-        props.allocType = cudaMemAllocationTypePinned;
-        props.handleTypes = cudaMemHandleTypeNone;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = device;
-        cudaMemPool_t pool;
-        cudaError_t e = cudaMemPoolCreate(&pool, &props);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
-        uint64_t keep = UINT64_MAX;  // keep freed scratch in the pool between calls
-        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
-        g_pools[device] = pool;
+// Per-call scratch comes from the device's stream-ordered memory pool
+// (cudaMallocAsync), which CUDA-graph capture turns into graph memory nodes.
+// The first use on a device keeps freed blocks in the pool between calls.
+int scratch_alloc(int device, void **out, size_t bytes, cudaStream_t s) {
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if ((int)g_pool_ready.size() <= device) g_pool_ready.resize((size_t)device + 1, 0);
+        if (!g_pool_ready[device]) {
+            cudaMemPool_t pool;
+            cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, device);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetDefaultMemPool");
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
+            g_pool_ready[device] = 1;
+        }
     }
-    *out = g_pools[device];
+    cudaError_t e = cudaMallocAsync(out, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
     return FP_OK;
 }
 
@@ -102,7 +101,7 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     int max_optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, f->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    const size_t budget = (size_t)max_optin - 64;  // static shared variables
+    const size_t budget = (size_t)max_optin - 256;  // leaves room for the static shared variables
     const int C = f->hdr.n_classes, F = f->hdr.n_features;
     int R = tile;
     while (R > 32 && smem_bytes(R, F, f->head_smem, C, warps, false) > budget) R -= 32;
@@ -121,6 +120,10 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     if (rc) return rc;
     rc = configure<true>(&g, g.smem_leaves, &g.grid_leaves);
     if (rc) return rc;
+    // the batched kernel may host any resident forest: allow it all of shared memory
+    cudaError_t e2 = cudaFuncSetAttribute(fp_traverse_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)budget);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute(batched)");
     f->R = g.R;
     f->threads = g.threads;
     f->refill = g.refill;
@@ -248,17 +251,14 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
     p.out_votes = out_votes;
     p.out_class = out_class;
     void *scratch = nullptr;
-    cudaMemPool_t pool = nullptr;
     cudaError_t e;
     if (h.n_passes > 1) {
         const size_t vote_bytes = out_votes ? 0 : (size_t)n * h.n_classes * 4;
         const size_t cnt_bytes = out_class ? (size_t)p.n_tiles * 4 : 0;
         const size_t bytes = ((vote_bytes + 255) & ~(size_t)255) + cnt_bytes;
         if (bytes) {
-            rc = scratch_pool(f->device, &pool);
+            rc = scratch_alloc(f->device, &scratch, bytes, s);
             if (rc) return rc;
-            e = cudaMallocFromPoolAsync(&scratch, bytes, pool, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
             e = cudaMemsetAsync(scratch, 0, bytes, s);
             if (e != cudaSuccess) { cudaFreeAsync(scratch, s); return cuda_fail(e, "cudaMemsetAsync(scratch)"); }
         }
@@ -346,9 +346,109 @@ extern "C" void fp_release(fp_device_forest *f) {
     delete f;
 }
 
-// Internal accessors for the batched entry point.
-const FpImageHeader *fp_dev_header(const fp_device_forest *f) { return &f->hdr; }
-TravParams fp_dev_params(const fp_device_forest *f, const float *X, int64_t n) { return base_params(f, X, n); }
-int fp_dev_device(const fp_device_forest *f) { return f->device; }
-int fp_dev_threads(const fp_device_forest *f) { return f->threads; }
-size_t fp_dev_smem(const fp_device_forest *f) { return f->smem_votes; }
+// One persistent launch over up to FP_MAX_BATCH (forest, batch) pairs.
+static int predict_batched_chunk(const fp_device_forest *const *forests, const fp_batch *batches, int32_t k,
+                                 cudaStream_t s) {
+    int device = -1;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int max_optin = 0;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const size_t budget = (size_t)max_optin - 256;
+    int warps = 1;
+    for (int32_t j = 0; j < k; ++j) warps = std::max(warps, forests[j]->threads / 32);
+
+    BatchParams bp;
+    memset(&bp, 0, sizeof bp);
+    size_t smem = 0;
+    size_t scratch_bytes = 256;  // the work counter, then per-batch accumulators and tile counters
+    std::vector<size_t> acc_off((size_t)k, 0), cnt_off((size_t)k, 0);
+    int32_t m = 0;
+    for (int32_t j = 0; j < k; ++j) {
+        const fp_device_forest *f = forests[j];
+        const fp_batch &bt = batches[j];
+        if (bt.n == 0 || (!bt.out_votes && !bt.out_class)) continue;
+        const FpImageHeader &h = f->hdr;
+        int R = f->R;
+        while (R > 32 && smem_bytes(R, h.n_features, f->head_smem, h.n_classes, warps, false) > budget) R -= 32;
+        const size_t need = smem_bytes(R, h.n_features, f->head_smem, h.n_classes, warps, false);
+        if (need > budget) {
+            fp_set_error("fp_predict_batched: batch %d does not fit shared memory with %d warps", j, warps);
+            return FP_EUNSUPPORTED;
+        }
+        smem = std::max(smem, need);
+        TravParams p = base_params(f, bt.X, bt.n);
+        p.R = R;
+        p.n_tiles = (bt.n + R - 1) / R;
+        p.n_passes = h.n_passes;
+        p.n_items = p.n_tiles * h.n_passes;
+        p.out_votes = bt.out_votes;
+        p.out_class = bt.out_class;
+        if (h.n_passes > 1) {
+            if (!bt.out_votes) {
+                acc_off[j] = scratch_bytes;
+                scratch_bytes += ((size_t)bt.n * h.n_classes * 4 + 255) & ~(size_t)255;
+            }
+            if (bt.out_class) {
+                cnt_off[j] = scratch_bytes;
+                scratch_bytes += ((size_t)p.n_tiles * 4 + 255) & ~(size_t)255;
+            }
+        }
+        bp.p[m] = p;
+        acc_off[m] = acc_off[j];
+        cnt_off[m] = cnt_off[j];
+        bp.item_begin[m + 1] = bp.item_begin[m] + p.n_items;
+        ++m;
+    }
+    bp.k = m;
+    if (m == 0) return FP_OK;
+    void *scratch = nullptr;
+    int rc = scratch_alloc(device, &scratch, scratch_bytes, s);
+    if (rc) return rc;
+    uint8_t *sc = static_cast<uint8_t *>(scratch);
+    e = cudaMemsetAsync(scratch, 0, scratch_bytes, s);
+    for (int32_t j = 0; j < m && e == cudaSuccess; ++j) {
+        TravParams &p = bp.p[j];
+        if (p.n_passes > 1) {
+            p.acc = p.out_votes ? p.out_votes : reinterpret_cast<uint32_t *>(sc + acc_off[j]);
+            if (p.out_class) p.tile_done = reinterpret_cast<uint32_t *>(sc + cnt_off[j]);
+            if (p.out_votes) e = cudaMemsetAsync(p.out_votes, 0, (size_t)p.n * p.C * 4, s);
+        }
+    }
+    bp.work = reinterpret_cast<unsigned long long *>(sc);
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_traverse_batched_kernel, 32 * warps, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(bp.item_begin[m], (int64_t)per_sm * sms));
+        fp_traverse_batched_kernel<<<(unsigned)grid, 32 * warps, smem, s>>>(bp);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp_predict_batched");
+    return FP_OK;
+}
+
+extern "C" int fp_predict_batched(const fp_device_forest *const *forests, const fp_batch *batches, int32_t k,
+                                  void *stream) {
+    if (k < 0 || (k > 0 && (!forests || !batches))) {
+        fp_set_error("fp_predict_batched: bad arguments");
+        return FP_EINVAL;
+    }
+    for (int32_t i = 0; i < k; ++i) {
+        if (!forests[i] || batches[i].n < 0 || (batches[i].n > 0 && !batches[i].X)) {
+            fp_set_error("fp_predict_batched: bad batch %d", i);
+            return FP_EINVAL;
+        }
+        int rc = check_device(forests[i]);
+        if (rc) return rc;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int32_t i = 0; i < k; i += FP_MAX_BATCH) {
+        int rc = predict_batched_chunk(forests + i, batches + i, std::min<int32_t>(FP_MAX_BATCH, k - i), s);
+        if (rc) return rc;
+    }
+    return FP_OK;
+}

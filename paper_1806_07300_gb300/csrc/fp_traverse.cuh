@@ -199,15 +199,47 @@ __device__ __forceinline__ void deep_step(const TravParams &p, const float *xs, 
     }
 }
 
+// CTA-wide state shared by the items a CTA runs.
+struct CtaShared {
+    uint64_t full[FP_NBUF];   // block staged (bulk copy done)
+    int task_next[FP_NBUF];   // next unclaimed task of the buffer's bin
+    int claim_done[FP_NBUF];  // warps done claiming the buffer's bin
+    int issued[FP_NBUF];      // bulk copies issued into the buffer
+    int last;
+    int abort;
+    long long next_item;
+};
+
+__device__ __forceinline__ void cta_init(CtaShared &sh) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < FP_NBUF; ++i) {
+            mbar_init(&sh.full[i], 1);
+            sh.issued[i] = 0;
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// After an abort, let this CTA's bulk copies land before it exits (bounded).
+__device__ __forceinline__ void cta_finish(CtaShared &sh) {
+    if (threadIdx.x == 0 && sh.abort) {
+        for (int i = 0; i < FP_NBUF; ++i) {
+            if (sh.issued[i] == 0) continue;
+            const uint32_t parity = (uint32_t)(sh.issued[i] - 1) & 1u;
+            for (int spin = 0; spin < FP_SPIN_LIMIT && !mbar_try_wait(&sh.full[i], parity); ++spin) {
+            }
+        }
+    }
+}
+
+// One work item (pass, observation tile) of one forest.  seq_base counts the
+// bins this CTA has staged before the item; every thread tracks it alike.
 template <bool LEAVES>
-__global__ void __launch_bounds__(1024, 1) fp_traverse_kernel(const TravParams p) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ __align__(8) uint64_t s_full[FP_NBUF];  // block staged (bulk copy done)
-    __shared__ int s_task_next[FP_NBUF];               // next unclaimed task of the buffer's bin
-    __shared__ int s_claim_done[FP_NBUF];              // warps done claiming the buffer's bin
-    __shared__ int s_issued[FP_NBUF];                  // bulk copies issued into the buffer
-    __shared__ int s_last;
-    __shared__ int s_abort;
+__device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh,
+                                         uint32_t &seq_base) {
     const int R = p.R, F = p.F, C = p.C;
     float *xs = reinterpret_cast<float *>(smem);
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
@@ -218,212 +250,231 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_kernel(const TravParams p
     uint2 *ring = reinterpret_cast<uint2 *>(smem + xs_bytes + FP_NBUF * p.head_smem + vote_bytes) + warp * FP_RING;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    if (tid == 0) {
-        for (int i = 0; i < FP_NBUF; ++i) {
-            mbar_init(&s_full[i], 1);
-            s_issued[i] = 0;
-        }
-        s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
-    __syncthreads();
-    uint32_t seq_base = 0;  // bins this CTA has staged before the current item
-
     // one thread: stage bin b as the CTA's seq-th bin
     auto issue = [&](int b, uint32_t seq) {
         const int buf = (int)(seq % FP_NBUF);
-        s_task_next[buf] = 0;
-        s_claim_done[buf] = 0;
-        s_issued[buf] += 1;
-        stage_block_bulk(p, b, hbuf0 + buf * p.head_smem, &s_full[buf]);
+        sh.task_next[buf] = 0;
+        sh.claim_done[buf] = 0;
+        sh.issued[buf] += 1;
+        stage_block_bulk(p, b, hbuf0 + buf * p.head_smem, &sh.full[buf]);
     };
 
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-        const int pass = (int)(item / p.n_tiles);
-        const int64_t tile = item - (int64_t)pass * p.n_tiles;
-        const int64_t row0 = tile * R;
-        const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
-        const FpPass ps = p.passes[pass];
-        const int nbins = ps.bin_end - ps.bin_begin;
+    const int pass = (int)(item / p.n_tiles);
+    const int64_t tile = item - (int64_t)pass * p.n_tiles;
+    const int64_t row0 = tile * R;
+    const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
+    const FpPass ps = p.passes[pass];
+    const int nbins = ps.bin_end - ps.bin_begin;
 
-        // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
-        {
-            const float *src = p.X + row0 * F;
-            const int total = rows * F;
-            for (int e = tid; e < total; e += blockDim.x) {
-                const int r = e / F;
-                cp_async4(xs + (e - r * F) * R + r, src + e);
-            }
-            cp_async_commit();
+    // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
+    {
+        const float *src = p.X + row0 * F;
+        const int total = rows * F;
+        for (int e = tid; e < total; e += blockDim.x) {
+            const int r = e / F;
+            cp_async4(xs + (e - r * F) * R + r, src + e);
         }
-        if (tid == 0 && !s_abort)
-            for (int i = 0; i < FP_NBUF && i < nbins; ++i) issue(ps.bin_begin + i, seq_base + i);
-        if (!LEAVES)
-            for (int i = tid; i < rows * C; i += blockDim.x) svotes[i] = 0;
-        cp_async_wait_all();
-        __syncthreads();
+        cp_async_commit();
+    }
+    if (tid == 0 && !sh.abort)
+        for (int i = 0; i < FP_NBUF && i < nbins; ++i) issue(ps.bin_begin + i, seq_base + i);
+    if (!LEAVES)
+        for (int i = tid; i < rows * C; i += blockDim.x) svotes[i] = 0;
+    cp_async_wait_all();
+    __syncthreads();
 
-        LaneTask L;
-        L.active = false;
-        L.r = 0;
-        L.t = 0;
-        L.ref = 0;
-        L.steps = 0;
-        L.tb = p.deep;
-        int head = 0, tail = 0;  // warp-uniform ring cursors
+    LaneTask L;
+    L.active = false;
+    L.r = 0;
+    L.t = 0;
+    L.ref = 0;
+    L.steps = 0;
+    L.tb = p.deep;
+    int head = 0, tail = 0;  // warp-uniform ring cursors
 
-        for (int bi = 0; bi < nbins; ++bi) {
-            const uint32_t seq = seq_base + bi;
-            const int buf = (int)(seq % FP_NBUF);
-            {  // wait until the bin's block has landed
-                const uint32_t parity = (seq / FP_NBUF) & 1u;
-                bool ok = false;
-                for (int spin = 0; spin < FP_SPIN_LIMIT; ++spin) {
-                    if (*(volatile int *)&s_abort) break;
-                    if (mbar_try_wait(&s_full[buf], parity)) {
-                        ok = true;
-                        break;
-                    }
-                }
-                if (!__all_sync(0xffffffffu, ok)) {
-                    if (lane == 0 && !*(volatile int *)&s_abort) {
-                        report(p.status, FP_ERR_FLAG_TIMEOUT);
-                        *(volatile int *)&s_abort = 1;
-                    }
+    for (int bi = 0; bi < nbins; ++bi) {
+        const uint32_t seq = seq_base + bi;
+        const int buf = (int)(seq % FP_NBUF);
+        {  // wait until the bin's block has landed
+            const uint32_t parity = (seq / FP_NBUF) & 1u;
+            bool ok = false;
+            for (int spin = 0; spin < FP_SPIN_LIMIT; ++spin) {
+                if (*(volatile int *)&sh.abort) break;
+                if (mbar_try_wait(&sh.full[buf], parity)) {
+                    ok = true;
                     break;
                 }
             }
-            const int b = ps.bin_begin + bi;
-            const FpBin bn = p.bins[b];
-            const int stride = bn.stride, nranks = bn.nranks, nexits = bn.nexits;
-            const int ntask = rows * bn.width;
-            const uint8_t *blk = hbuf0 + buf * p.head_smem;
-            const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
-            const uint32_t *hexit = reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * 8);
-            volatile int *next = &s_task_next[buf];
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0 && !*(volatile int *)&sh.abort) {
+                    report(p.status, FP_ERR_FLAG_TIMEOUT);
+                    *(volatile int *)&sh.abort = 1;
+                }
+                break;
+            }
+        }
+        const int b = ps.bin_begin + bi;
+        const FpBin bn = p.bins[b];
+        const int stride = bn.stride, nranks = bn.nranks, nexits = bn.nexits;
+        const int ntask = rows * bn.width;
+        const uint8_t *blk = hbuf0 + buf * p.head_smem;
+        const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
+        const uint32_t *hexit = reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * 8);
+        volatile int *next = &sh.task_next[buf];
 
-            for (;;) {
-                if (*next >= ntask) break;  // the bin's tasks are all claimed
-                if (tail - head <= p.refill) {
-                    // burst: 32 consecutive tasks through the head, all lanes together
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&s_task_next[buf], 32);
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (base >= ntask) break;
-                    const bool my = lane < ntask - base;
-                    const int task = base + lane;
-                    const int k2 = my ? task / rows : 0;
-                    const int r2 = my ? task - k2 * rows : 0;
-                    uint32_t hr = 0;  // head rank, then nranks + exit index
-                    bool busy = my;
-                    int guard = 0;
-                    while (__any_sync(0xffffffffu, busy)) {
-                        if (busy) {
-                            const uint2 nd = hnode[hr * stride + k2];
-                            const uint32_t m = nd.y;
-                            hr = xs[(m >> 22) * R + r2] <= __uint_as_float(nd.x) ? (m & FP_TARGET_MASK)
-                                                                                   : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
-                            busy = hr < (uint32_t)nranks;
-                            if (++guard > nranks && busy) {  // a path visits each rank at most once
-                                report(p.status, FP_ERR_FLAG_DEVICE);
-                                busy = false;
-                                hr = (uint32_t)(nranks + nexits);
-                            }
+        for (;;) {
+            if (*next >= ntask) break;  // the bin's tasks are all claimed
+            if (tail - head <= p.refill) {
+                // burst: 32 consecutive tasks through the head, all lanes together
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&sh.task_next[buf], 32);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= ntask) break;
+                const bool my = lane < ntask - base;
+                const int task = base + lane;
+                const int k2 = my ? task / rows : 0;
+                const int r2 = my ? task - k2 * rows : 0;
+                uint32_t hr = 0;  // head rank, then nranks + exit index
+                bool busy = my;
+                int guard = 0;
+                while (__any_sync(0xffffffffu, busy)) {
+                    if (busy) {
+                        const uint2 nd = hnode[hr * stride + k2];
+                        const uint32_t m = nd.y;
+                        hr = xs[(m >> 22) * R + r2] <= __uint_as_float(nd.x) ? (m & FP_TARGET_MASK)
+                                                                               : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
+                        busy = hr < (uint32_t)nranks;
+                        if (++guard > nranks && busy) {  // a path visits each rank at most once
+                            report(p.status, FP_ERR_FLAG_DEVICE);
+                            busy = false;
+                            hr = (uint32_t)(nranks + nexits);
                         }
                     }
-                    const uint32_t e = hr - (uint32_t)nranks;
-                    const uint32_t er = (my && e < (uint32_t)nexits) ? hexit[e * stride + k2] : FP_NO_CLASS;
-                    const int t2 = bn.first_tree + k2;
-                    if (my && (er & FP_REF_LEAF)) {
-                        int32_t leaf_id = -1;
-                        if (LEAVES && e < (uint32_t)nexits) leaf_id = p.pheads[(bn.phead_off >> 2) + e * stride + k2];
-                        finish<LEAVES>(p, svotes, row0, r2, t2, er & 0x7FFFFFFFu, leaf_id);
-                    }
-                    const bool push = my && !(er & FP_REF_LEAF);
-                    const unsigned pm = __ballot_sync(0xffffffffu, push);
-                    if (push)
-                        ring[(tail + __popc(pm & lt_mask)) & (FP_RING - 1)] =
-                            make_uint2(er, (uint32_t)r2 | ((uint32_t)t2 << 11));
-                    tail += __popc(pm);
-                    __syncwarp();
                 }
-                pop_tasks(p, ring, head, tail, L, lt_mask);
-                if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
+                const uint32_t e = hr - (uint32_t)nranks;
+                const uint32_t er = (my && e < (uint32_t)nexits) ? hexit[e * stride + k2] : FP_NO_CLASS;
+                const int t2 = bn.first_tree + k2;
+                if (my && (er & FP_REF_LEAF)) {
+                    int32_t leaf_id = -1;
+                    if (LEAVES && e < (uint32_t)nexits) leaf_id = p.pheads[(bn.phead_off >> 2) + e * stride + k2];
+                    finish<LEAVES>(p, svotes, row0, r2, t2, er & 0x7FFFFFFFu, leaf_id);
+                }
+                const bool push = my && !(er & FP_REF_LEAF);
+                const unsigned pm = __ballot_sync(0xffffffffu, push);
+                if (push)
+                    ring[(tail + __popc(pm & lt_mask)) & (FP_RING - 1)] =
+                        make_uint2(er, (uint32_t)r2 | ((uint32_t)t2 << 11));
+                tail += __popc(pm);
+                __syncwarp();
             }
-            // this warp reads the bin's block no more; the last warp refills the buffer
-            __syncwarp();
-            if (lane == 0) {
-                const int done = atomicAdd(&s_claim_done[buf], 1);
-                if (done == nwarps - 1 && bi + FP_NBUF < nbins && !*(volatile int *)&s_abort)
-                    issue(ps.bin_begin + bi + FP_NBUF, seq + FP_NBUF);
-            }
-            __syncwarp();
-        }
-        seq_base += (uint32_t)nbins;
-        const bool aborted = *(volatile int *)&s_abort != 0;
-        // drain: the item's last pending and running tasks
-        for (; !aborted;) {
-            __syncwarp();
             pop_tasks(p, ring, head, tail, L, lt_mask);
-            if (!__any_sync(0xffffffffu, L.active)) break;
             if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
         }
-        __syncthreads();
+        // this warp reads the bin's block no more; the last warp refills the buffer
+        __syncwarp();
+        if (lane == 0) {
+            const int done = atomicAdd(&sh.claim_done[buf], 1);
+            if (done == nwarps - 1 && bi + FP_NBUF < nbins && !*(volatile int *)&sh.abort)
+                issue(ps.bin_begin + bi + FP_NBUF, seq + FP_NBUF);
+        }
+        __syncwarp();
+    }
+    seq_base += (uint32_t)nbins;
+    const bool aborted = *(volatile int *)&sh.abort != 0;
+    // drain: the item's last pending and running tasks
+    for (; !aborted;) {
+        __syncwarp();
+        pop_tasks(p, ring, head, tail, L, lt_mask);
+        if (!__any_sync(0xffffffffu, L.active)) break;
+        if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
+    }
+    __syncthreads();
 
-        // 5. votes and class
-        if (!LEAVES && !*(volatile int *)&s_abort) {
-            if (p.n_passes == 1) {
-                if (p.out_votes) {
-                    uint32_t *dst = p.out_votes + row0 * C;
-                    for (int i = tid; i < rows * C; i += blockDim.x) dst[i] = svotes[i];
+    // 5. votes and class
+    if (!LEAVES && !*(volatile int *)&sh.abort) {
+        if (p.n_passes == 1) {
+            if (p.out_votes) {
+                uint32_t *dst = p.out_votes + row0 * C;
+                for (int i = tid; i < rows * C; i += blockDim.x) dst[i] = svotes[i];
+            }
+            if (p.out_class) {
+                for (int rr = tid; rr < rows; rr += blockDim.x) {
+                    const uint32_t *v = svotes + rr * C;
+                    int best = 0;
+                    uint32_t bv = v[0];
+                    for (int c = 1; c < C; ++c)
+                        if (v[c] > bv) { bv = v[c]; best = c; }
+                    p.out_class[row0 + rr] = best;
                 }
-                if (p.out_class) {
+            }
+        } else {
+            uint32_t *dst = p.acc + row0 * C;
+            for (int i = tid; i < rows * C; i += blockDim.x) {
+                const uint32_t v = svotes[i];
+                if (v) atomicAdd(dst + i, v);
+            }
+            if (p.out_class) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) sh.last = atomicAdd(p.tile_done + tile, 1u) == (unsigned)(p.n_passes - 1);
+                __syncthreads();
+                if (sh.last) {
+                    __threadfence();
                     for (int rr = tid; rr < rows; rr += blockDim.x) {
-                        const uint32_t *v = svotes + rr * C;
+                        const uint32_t *v = dst + rr * C;
                         int best = 0;
-                        uint32_t bv = v[0];
-                        for (int c = 1; c < C; ++c)
-                            if (v[c] > bv) { bv = v[c]; best = c; }
+                        uint32_t bv = __ldcg(v);
+                        for (int c = 1; c < C; ++c) {
+                            const uint32_t w = __ldcg(v + c);
+                            if (w > bv) { bv = w; best = c; }
+                        }
                         p.out_class[row0 + rr] = best;
                     }
                 }
-            } else {
-                uint32_t *dst = p.acc + row0 * C;
-                for (int i = tid; i < rows * C; i += blockDim.x) {
-                    const uint32_t v = svotes[i];
-                    if (v) atomicAdd(dst + i, v);
-                }
-                if (p.out_class) {
-                    __threadfence();
-                    __syncthreads();
-                    if (tid == 0) s_last = atomicAdd(p.tile_done + tile, 1u) == (unsigned)(p.n_passes - 1);
-                    __syncthreads();
-                    if (s_last) {
-                        __threadfence();
-                        for (int rr = tid; rr < rows; rr += blockDim.x) {
-                            const uint32_t *v = dst + rr * C;
-                            int best = 0;
-                            uint32_t bv = __ldcg(v);
-                            for (int c = 1; c < C; ++c) {
-                                const uint32_t w = __ldcg(v + c);
-                                if (w > bv) { bv = w; best = c; }
-                            }
-                            p.out_class[row0 + rr] = best;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();  // the next item reuses shared memory
-    }
-    // after an abort, let this CTA's bulk copies land before it exits (bounded)
-    if (tid == 0 && s_abort) {
-        for (int i = 0; i < FP_NBUF; ++i) {
-            if (s_issued[i] == 0) continue;
-            const uint32_t parity = (uint32_t)(s_issued[i] - 1) & 1u;
-            for (int spin = 0; spin < FP_SPIN_LIMIT && !mbar_try_wait(&s_full[i], parity); ++spin) {
             }
         }
     }
+    __syncthreads();  // the next item reuses shared memory
+
+}
+
+template <bool LEAVES>
+__global__ void __launch_bounds__(1024, 1) fp_traverse_kernel(const TravParams p) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ CtaShared sh;
+    cta_init(sh);
+    uint32_t seq_base = 0;
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<LEAVES>(p, item, smem, sh, seq_base);
+    cta_finish(sh);
+}
+
+// Several forests and batches in one persistent launch: the work items of
+// all batches form one list (batch by batch, pass-major within a batch),
+// handed out to CTAs through a global counter so uneven batches balance.
+#define FP_MAX_BATCH 32
+
+struct BatchParams {
+    int32_t k;
+    int64_t item_begin[FP_MAX_BATCH + 1];
+    TravParams p[FP_MAX_BATCH];
+    unsigned long long *work;  // zeroed before the launch
+};
+
+__global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __grid_constant__ BatchParams bp) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ CtaShared sh;
+    cta_init(sh);
+    uint32_t seq_base = 0;
+    const int64_t total = bp.item_begin[bp.k];
+    for (;;) {
+        if (threadIdx.x == 0) sh.next_item = (long long)atomicAdd(bp.work, 1ull);
+        __syncthreads();
+        const int64_t item = sh.next_item;
+        __syncthreads();
+        if (item >= total) break;
+        int j = 0;
+        while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
+        run_item<false>(bp.p[j], item - bp.item_begin[j], smem, sh, seq_base);
+    }
+    cta_finish(sh);
 }
