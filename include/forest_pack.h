@@ -167,6 +167,28 @@ int fp_configure(fp_device_forest *forest, const fp_pack_params *params);
 int fp_predict(const fp_device_forest *forest, const float *X, int64_t n, uint32_t *out_votes, int32_t *out_class,
                void *stream);
 
+/* fp_predict without any device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory while
+ * they classify -- a serving loop that runs under a fixed device-memory
+ * budget and must not grow or fragment the heap, code that runs while it
+ * holds its own allocator's lock, or code that must not reach the driver's
+ * allocation path, which can synchronise the device.
+ * Arguments, outputs and errors are those of fp_predict.  A forest swept in
+ * several passes needs scratch (a vote accumulator when out_votes is NULL and
+ * one counter per observation tile when out_class is given); here it comes
+ * from one fixed 16 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  A call whose scratch
+ * would exceed 16 MiB returns FP_EINVAL before enqueuing anything (pass
+ * out_votes, split the batch, or use fp_predict).  The first call on a device
+ * looks up the array's device address, so make it before any CUDA-graph
+ * stream capture.  All calls on a device share its one array, which keeps
+ * the last call's contents; each call clears the part it uses.  Calls whose
+ * work overlaps on the GPU (for instance on two streams) race on the array
+ * and must be ordered by the caller.  Nothing is allocated or freed: no
+ * cudaMalloc, cudaFree, cudaMallocAsync or library allocator. */
+int fp_predict_noalloc(const fp_device_forest *forest, const float *X, int64_t n, uint32_t *out_votes,
+                       int32_t *out_class, void *stream);
+
 /* Parity mode: the leaf each observation reaches in each tree.
  *   out_leaf   device, [n][n_trees] int32, tree-local node id of the leaf in
  *              the fp_forest_desc the forest was packed from

@@ -68,7 +68,7 @@ class fp_batch(ctypes.Structure):
 
 # every symbol include/forest_pack.h declares
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
-           "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
+           "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
            "fp_plain_release"]
 
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
                 "fp_upload": ([P, P, ctypes.POINTER(P)], ctypes.c_int),
                 "fp_predict": ([P, P, i64, P, P, P], ctypes.c_int),
                 "fp_configure": ([P, ctypes.POINTER(fp_pack_params)], ctypes.c_int),
+                "fp_predict_noalloc": ([P, P, i64, P, P, P], ctypes.c_int),
                 "fp_predict_leaves": ([P, P, i64, P, P], ctypes.c_int),
                 "fp_predict_batched": ([P, P, i32, P], ctypes.c_int),
                 "fp_sync_status": ([P, P], ctypes.c_int),
@@ -204,6 +205,17 @@ def fp_predict(forest: "DeviceForest", X, out_votes=None, out_class=None, stream
     vp = _dptr(out_votes, _torch().int32, (n, info["n_classes"]), "out_votes") if out_votes is not None else None
     cp = _dptr(out_class, _torch().int32, (n,), "out_class") if out_class is not None else None
     _check(lib().fp_predict(forest.handle, xp, n, vp, cp, _stream_ptr(stream)), "fp_predict")
+
+
+def fp_predict_noalloc(forest: "DeviceForest", X, out_votes=None, out_class=None, stream=None) -> None:
+    """fp_predict that allocates no device memory (scratch from a fixed
+    16 MiB array inside the library; see include/forest_pack.h)."""
+    n = X.shape[0]
+    info = forest.info
+    xp = _dptr(X, _torch().float32, (n, info["n_features"]), "X")
+    vp = _dptr(out_votes, _torch().int32, (n, info["n_classes"]), "out_votes") if out_votes is not None else None
+    cp = _dptr(out_class, _torch().int32, (n,), "out_class") if out_class is not None else None
+    _check(lib().fp_predict_noalloc(forest.handle, xp, n, vp, cp, _stream_ptr(stream)), "fp_predict_noalloc")
 
 
 def fp_predict_leaves(forest: "DeviceForest", X, out_leaf, stream=None) -> None:

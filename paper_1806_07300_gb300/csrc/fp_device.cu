@@ -281,6 +281,85 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
     return FP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// fp_predict_noalloc: fp_predict for callers that must not allocate device
+// memory.  The scratch that a forest swept in several passes needs (a vote
+// accumulator when no votes buffer is given, one counter per observation
+// tile when classes are asked for) lives in this fixed array instead of the
+// stream-ordered pool.  Every GPU that loads the library holds the array
+// until the process exits.
+#define FP_NOALLOC_SCRATCH_BYTES (16u << 20)
+static __device__ __align__(256) unsigned char fp_noalloc_scratch[FP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::vector<void *> g_noalloc_ptr;  // device address of the array, per device (set up once)
+
+// Host code cannot use the array's name as a device address: look the
+// address up once per device, with that device current.
+int noalloc_scratch(int device, void **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_ptr.size() <= device) g_noalloc_ptr.resize((size_t)device + 1, nullptr);
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, fp_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(fp_noalloc_scratch)");
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = g_noalloc_ptr[device];
+    return FP_OK;
+}
+}  // namespace
+
+extern "C" int fp_predict_noalloc(const fp_device_forest *f, const float *X, int64_t n, uint32_t *out_votes,
+                                  int32_t *out_class, void *stream) {
+    if (!f || n < 0 || (n > 0 && !X)) {
+        fp_set_error("fp_predict_noalloc: bad arguments");
+        return FP_EINVAL;
+    }
+    if (n == 0 || (!out_votes && !out_class)) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const FpImageHeader &h = f->hdr;
+    TravParams p = base_params(f, X, n);
+    p.n_passes = h.n_passes;
+    p.n_items = p.n_tiles * h.n_passes;
+    p.out_votes = out_votes;
+    p.out_class = out_class;
+    cudaError_t e;
+    if (h.n_passes > 1) {
+        const size_t vote_bytes = out_votes ? 0 : (size_t)n * h.n_classes * 4;
+        const size_t cnt_bytes = out_class ? (size_t)p.n_tiles * 4 : 0;
+        const size_t bytes = ((vote_bytes + 255) & ~(size_t)255) + cnt_bytes;
+        if (bytes > FP_NOALLOC_SCRATCH_BYTES) {
+            fp_set_error("fp_predict_noalloc: %lld rows need %zu bytes of scratch, more than the fixed %u; pass "
+                         "out_votes, split the batch, or use fp_predict",
+                         (long long)n, bytes, FP_NOALLOC_SCRATCH_BYTES);
+            return FP_EINVAL;
+        }
+        void *scratch = nullptr;
+        rc = noalloc_scratch(f->device, &scratch);
+        if (rc) return rc;
+        if (bytes) {
+            e = cudaMemsetAsync(scratch, 0, bytes, s);  // the last call's counts must not leak in
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(noalloc scratch)");
+        }
+        uint8_t *sc = static_cast<uint8_t *>(scratch);
+        p.acc = out_votes ? out_votes : reinterpret_cast<uint32_t *>(sc);
+        p.tile_done = reinterpret_cast<uint32_t *>(sc + ((vote_bytes + 255) & ~(size_t)255));
+        if (out_votes) {
+            e = cudaMemsetAsync(out_votes, 0, (size_t)n * h.n_classes * 4, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(out_votes)");
+        }
+    }
+    const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
+    fp_traverse_kernel<false><<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
+    return FP_OK;
+}
+
 extern "C" int fp_predict_leaves(const fp_device_forest *f, const float *X, int64_t n, int32_t *out_leaf,
                                  void *stream) {
     if (!f || n < 0 || (n > 0 && (!X || !out_leaf))) {
