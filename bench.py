@@ -1,23 +1,35 @@
 """Benchmark: observations/s of packed-forest classification on GB300.
 
-One step = one pass of the whole hot path (interleaved levels, Stat regions,
-votes, argmax) over one batch of synthetic observations resident in HBM:
-fp_predict(forest, X[n], out_votes, out_class).  Default workload: the
-HBM-resident forest (256 CART trees of ~8*10^4 internal nodes, forest far
-larger than L2) classifying 4,000,000 rows of 28 FP32 features.
+One step = one pass of the whole hot path (the interleaved heads in shared
+memory, the super-node walks, votes, argmax) over one batch of synthetic
+observations resident in HBM: fp_predict(forest, X[n], out_votes, out_class).
+
+Workloads (--workload):
+  hbm      (default) the HBM-resident forest -- 256 CART trees of ~8*10^4
+           internal nodes, forest far larger than L2 -- classifying
+           4,000,000 rows of 28 FP32 features;
+  image    128 trees, 784 features, 10 classes, 1,000,000 rows;
+  tiny     16 trees, 16 features, 4 classes, 10,000 rows;
+  batched  8 forests (32..512 trees) and uneven batches (1..100,000 rows) in
+           one persistent launch replayed from a CUDA graph;
+  serving  4 resident forests behind the continuous-batching server, Poisson
+           arrivals at 2k/5k/10k/20k requests/s; p50/p99 latency.
 
 Prints one JSON line (rank 0).  Besides the headline value it reports the
-plain breadth-first GPU baseline on the same inputs (faster of its two thread
-orders), the end-to-end figure through host buffers, the roofline of the
-traversal kernel, and the CPU oracle timed on a bounded sample.
+plain breadth-first GPU baseline on the same inputs (the faster of its two
+thread orders), the end-to-end figure through host buffers, the roofline of
+the traversal kernel against the measured HBM copy bandwidth and a measured
+L2 read bandwidth, and the CPU oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl packed|reference]
-                    [--workload hbm|image|tiny] [--rows N]
+                    [--workload hbm|image|tiny|batched|serving] [--rows N]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,7 +48,16 @@ WORKLOADS = {
     "hbm": dict(rows=4_000_000, desc="HBM-resident forest: 256 trees, 28 features, 2 classes, 500k training rows"),
     "image": dict(rows=1_000_000, desc="image-shaped: 128 trees, 784 features, 10 classes, 60k training rows"),
     "tiny": dict(rows=10_000, desc="tiny: 16 trees, 16 features, 4 classes, 2k training rows"),
+    "batched": dict(rows=0, desc="8 forests (32..512 trees, 8..200 features, 2..50 classes), batches 1..100k rows, "
+                                 "one persistent launch replayed from a CUDA graph"),
+    "serving": dict(rows=0, desc="4 resident forests (tiny, image, hbm, 64-tree 50-class 100-feature), Poisson "
+                                 "arrivals, rows/request LogNormal(ln 32, 1.5) clipped to [1, 4096]"),
 }
+
+# Layout and launch candidates timed by the autotuner for the default workload
+# (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
+HBM_LAYOUTS = [(3, 8), (2, 8), (1, 9), (16, 4), (64, 2)]
+HBM_LAUNCHES = [(768, 32, 32), (1024, 32, 16)]
 
 
 def parse():
@@ -49,11 +70,14 @@ def parse():
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--bin-size", type=int, default=0)
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--pass-bytes", type=int, default=0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -76,8 +100,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -115,13 +138,36 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_fingerprint() -> str:
+    """Hash of the sources that decide the traversal kernel's memory traffic."""
+    h = hashlib.sha1()
+    for name in ("fp_traverse.cuh", "fp_pack.cpp", "fp_internal.h", "fp_device.cu"):
+        with open(os.path.join(ROOT, "paper_1806_07300_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, params: dict, rows: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `rows`
+    (traffic grows with the rows swept), or None when the kernel or the
+    parameters changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("fingerprint") != kernel_fingerprint() or d.get("params") != params:
+        return None
+    return d["dram_bytes_per_launch"] * rows / d["rows"]
+
+
 def cpu_sample(forest, X, target_s: float, threads: int):
     """Oracle on a bounded prefix of the workload's rows: returns obs/s,
-    visits per observation and the sample size."""
+    visits per observation, the sample size and the seconds taken."""
     import oracle
     n = min(2000, X.shape[0])
     t0 = time.perf_counter()
-    r = oracle.predict(forest, X[:n], leaves=False, votes=False, threads=threads)
+    oracle.predict(forest, X[:n], leaves=False, votes=False, threads=threads)
     dt = max(time.perf_counter() - t0, 1e-6)
     m = int(min(X.shape[0], max(n, n * target_s / dt)))
     t0 = time.perf_counter()
@@ -137,31 +183,38 @@ def dist_setup(args):
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        if args.impl == "packed":
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if args.impl == "packed" else "gloo")
     return ws, rank, local
+
+
+def base_line(args, ws, value, total_ms, config, dtype="f32"):
+    return {"metric": METRIC, "value": value, "unit": "observations/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded generators; CART forests trained at start)", "config": config}
 
 
 # --------------------------------------------------------------- reference
 
 def run_reference(args, ws, rank):
     """The oracle as it stands, on the host cores, timed per step on a bounded
-    sample of the same workload."""
+    sample of the same workload (rank 0 only)."""
     if rank != 0:
         return
     import datagen
     import oracle
-    name = args.workload
+    name = args.workload if args.workload in ("hbm", "image", "tiny") else "hbm"
     forest = datagen.forest(name)
     n_full = args.rows or WORKLOADS[name]["rows"]
     threads = oracle.default_threads()
-    # size one step for ~2 s of CPU work so the whole run stays within minutes
     probe_rows = min(2000, n_full)
     X, _ = datagen.test_rows(name, probe_rows)
     t0 = time.perf_counter()
     oracle.predict(forest, X, leaves=False, votes=False, threads=threads)
     dt = max(time.perf_counter() - t0, 1e-6)
-    m = int(min(n_full, max(probe_rows, probe_rows * 2.0 / dt)))
+    m = int(min(n_full, max(probe_rows, probe_rows * 2.0 / dt)))  # ~2 s of CPU work per step
     X, _ = datagen.test_rows(name, m)
     for _ in range(args.warmup):
         oracle.predict(forest, X, leaves=False, votes=False, threads=threads)
@@ -172,17 +225,40 @@ def run_reference(args, ws, rank):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = m * args.steps / total
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "observations/s",
-           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": name, "desc": WORKLOADS[name]["desc"], "rows_per_step": m, "n_trees": forest.n_trees},
-           "cpu_baseline": {"value": value, "unit": "observations/s", "cores": threads, "kind": "oracle",
-                            "sample": f"first {m} of the workload's {n_full} test rows per step"},
-           "e2e": {"value": value, "unit": "observations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    out = base_line(args, ws, value, 1e3 * total,
+                    {"workload": name, "desc": WORKLOADS[name]["desc"], "rows_per_step": m,
+                     "n_trees": forest.n_trees})
+    out["impl"] = "reference"
+    out["cpu_baseline"] = {"value": value, "unit": "observations/s", "cores": threads, "kind": "oracle",
+                           "sample": f"first {m} of the workload's {n_full} test rows per step"}
+    out["e2e"] = {"value": value, "unit": "observations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     print(json.dumps(out))
 
 
-# ------------------------------------------------------------------ packed
+# ------------------------------------------------------------- single forest
+
+def tuned_forest(args, forest, X, name):
+    import paper_1806_07300_gb300 as fp
+    from paper_1806_07300_gb300 import autotune as at
+    explicit = args.bin_size or args.depth >= 0 or args.tile or args.warps or args.refill
+    tuning = None
+    if explicit or args.no_autotune:
+        params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes)
+        df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
+        df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill)
+    else:
+        sample = X[: min(X.shape[0], 1 << 20)]
+        layouts = HBM_LAYOUTS if name == "hbm" else None
+        launches = HBM_LAUNCHES if name == "hbm" else None
+        best = at.autotune(forest, sample, layouts=layouts, launches=launches)
+        tuning = {k: best[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+        tuning["candidates"] = len([r for r in best["table"] if "ms" in r])
+        df = fp.fp_upload(fp.fp_pack_forest(forest, bin_size=best["bin_size"],
+                                            interleave_depth=best["interleave_depth"]))
+        df.configure(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"],
+                     refill_lanes=best["refill_lanes"])
+    return df, tuning
+
 
 def run_packed(args, ws, rank, local):
     import torch
@@ -196,19 +272,13 @@ def run_packed(args, ws, rank, local):
     forest = datagen.forest(name)
     Xh, _ = datagen.test_rows(name, n)
     F, C, T = forest.n_features, forest.n_classes, forest.n_trees
-
-    pk = fp.fp_pack_forest(forest, bin_size=args.bin_size, interleave_depth=args.depth, obs_tile=args.tile,
-                           warps_per_cta=args.warps, pass_bytes=args.pass_bytes)
-    df = fp.fp_upload(pk)
+    X = torch.from_numpy(Xh).to(dev)
+    df, tuning = tuned_forest(args, forest, X, name)
     info = df.info
     stream = torch.cuda.Stream(device=dev)
-    X = torch.from_numpy(Xh).to(dev)
     votes = torch.empty((n, C), dtype=torch.int32, device=dev)
     cls = torch.empty((n,), dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
-
-    def step():
-        fp.fp_predict(df, X, votes, cls, stream=stream)
 
     def barrier():
         if ws > 1:
@@ -216,7 +286,7 @@ def run_packed(args, ws, rank, local):
             dist.barrier()
 
     for _ in range(args.warmup):
-        step()
+        fp.fp_predict(df, X, votes, cls, stream=stream)
     torch.cuda.synchronize()
     status = df.sync_status(stream)
     if status != fp.FP_OK:
@@ -232,7 +302,7 @@ def run_packed(args, ws, rank, local):
     start.record(stream)
     for i in range(args.steps):
         ev[i][0].record(stream)
-        step()
+        fp.fp_predict(df, X, votes, cls, stream=stream)
         ev[i][1].record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
@@ -265,14 +335,15 @@ def run_packed(args, ws, rank, local):
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / ks
-            ok = bool(torch.equal(pc, cls))
-            cand = {"order": oname, "value": n / (ms / 1e3), "ms_per_step": ms, "same_classes": ok}
+            cand = {"order": oname, "value": n / (ms / 1e3), "ms_per_step": ms,
+                    "same_classes": bool(torch.equal(pc, cls))}
             if best is None or cand["value"] > best["value"]:
                 best = cand
         plain = dict(best, unit="observations/s", layout_bytes=pf.nbytes())
         pf.release()
+        del pv, pc
 
-    # end to end through host buffers: pinned X in, classes out, every step
+    # end to end through host buffers: pinned rows in, classes out, every step
     Xpin = torch.from_numpy(Xh).pin_memory()
     cls_host = torch.empty((n,), dtype=torch.int32).pin_memory()
     Xd2 = torch.empty_like(X)
@@ -290,10 +361,10 @@ def run_packed(args, ws, rank, local):
     e2e_ms = a.elapsed_time(b) / e2e_steps
     e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "observations/s", "h2d_bytes_per_step": int(Xpin.numel() * 4),
            "d2h_bytes_per_step": int(cls_host.numel() * 4), "ms_per_step": e2e_ms}
+    l2_gbs = fp.fp_l2_read_probe(64 << 20, 40, stream=stream)
 
     if rank != 0:
         return
-    # CPU oracle on a bounded sample; its visit count gives the algorithmic bytes
     import oracle
     threads = oracle.default_threads()
     cpu_value, visits_per_obs, m, cpu_s = cpu_sample(forest, Xh, args.cpu_seconds, threads)
@@ -301,31 +372,153 @@ def run_packed(args, ws, rank, local):
     avg_launch_ms = statistics.mean(per_launch_ms)
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    out = {
-        "metric": METRIC, "value": value, "unit": "observations/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators; CART forest trained at start)",
-        "config": {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
-                   "n_classes": C, "bin_size": info["bin_size"], "interleave_depth": info["interleave_depth"],
-                   "obs_tile": info["obs_tile"], "warps_per_cta": info["warps_per_cta"], "passes": info["passes"],
-                   "forest_bytes": info["total_bytes"], "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (rows %.0f MB, forest %.0f MB); no flush" %
-                         (Xh.nbytes / 1e6, info["total_bytes"] / 1e6)},
+    params = {k: info[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+    traffic = profiled_traffic(name, params, n)
+    out = base_line(args, ws, value, total_ms,
+                    {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
+                     "n_classes": C, **params, "passes": info["passes"], "forest_bytes": info["total_bytes"],
+                     "autotuned": tuning is not None, "parallelism": f"replicas x{ws}",
+                     "l2": "inputs larger than L2 (rows %.0f MB, forest %.0f MB); no flush" %
+                           (Xh.nbytes / 1e6, info["total_bytes"] / 1e6)})
+    out.update({
         "plain_baseline": plain,
         "packed_vs_plain": (value / ws / plain["value"]) if plain else None,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "fp_traverse_kernel<false>", "avg_launch_ms": avg_launch_ms,
-                     "bytes_per_obs": bytes_per_obs, "visits_per_obs": visits_per_obs,
-                     "node_visits_per_s": visits_per_obs * n / (avg_launch_ms / 1e3)},
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "fp_traverse_kernel<false>",
+                     "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
+                     "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_obs * n / (avg_launch_ms / 1e3),
+                     "l2": {"peak": l2_gbs, "achieved": achieved, "frac": achieved / l2_gbs, "unit": "GB/s",
+                            "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"}},
         "cpu_baseline": {"value": cpu_value, "unit": "observations/s", "cores": threads, "kind": "oracle",
                          "sample": f"first {m} of {n} rows ({cpu_s:.1f} s)"},
         "clocks": clk,
-    }
+    })
     print(json.dumps(out))
     df.release()
+
+
+# ------------------------------------------------------------------ batched
+
+def run_batched(args, ws, rank, local):
+    """The batched workload: one persistent launch over 8 forests and uneven
+    batches, captured once in a CUDA graph and replayed every step."""
+    import torch
+    import datagen
+    import paper_1806_07300_gb300 as fp
+    from paper_1806_07300_gb300 import autotune as at
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    names = [f"batched{k}" for k in range(len(datagen.BATCHED_SPECS))]
+    forests = [datagen.forest(nm) for nm in names]
+    sizes = datagen.batch_sizes()
+    Xh = [datagen.test_rows(nm, s)[0] for nm, s in zip(names, sizes)]
+    Xs = [torch.from_numpy(x).to(dev) for x in Xh]
+    dfs = []
+    for f, x in zip(forests, Xs):
+        if x.shape[0] >= 4096:
+            d, _ = at.upload_tuned(f, x, layouts=at.candidate_layouts(f.n_trees, max_layouts=4),
+                                   launches=[(0, 32, 32)])
+        else:
+            d = fp.fp_upload(fp.fp_pack_forest(f))
+        dfs.append(d)
+    votes = [torch.empty((x.shape[0], f.n_classes), dtype=torch.int32, device=dev) for f, x in zip(forests, Xs)]
+    cls = [torch.empty((x.shape[0],), dtype=torch.int32, device=dev) for x in Xs]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        fp.fp_predict_batched(dfs, Xs, votes, cls, stream=stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fp.fp_predict_batched(dfs, Xs, votes, cls, stream=torch.cuda.current_stream())
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = a.elapsed_time(b)
+    rows = sum(sizes)
+    value = ws * rows * args.steps / (total_ms / 1e3)
+    if rank != 0:
+        return
+    out = base_line(args, ws, value, total_ms,
+                    {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
+                     "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
+                     "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
+    out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
+                "e2e": None, "roofline": None, "cpu_baseline": None})
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ serving
+
+def run_serving(args, ws, rank, local):
+    """Poisson request streams against the continuous-batching server."""
+    import torch
+    import datagen
+    from paper_1806_07300_gb300.serving import ForestServer, latency_summary
+
+    torch.cuda.set_device(local)
+    names = {"tiny": "tiny", "image": "image", "hbm": "hbm", "wide": "wide"}
+    forests = {k: datagen.forest(v) for k, v in names.items()}
+    pools = {k: datagen.test_rows(v, 200_000 if k != "tiny" else 10_000)[0] for k, v in names.items()}
+    srv = ForestServer(device=local, slots=3, max_rows=1 << 17)
+    for k, f in forests.items():
+        srv.add_forest(k, f)
+    rng = np.random.Generator(np.random.PCG64(11))
+    keys = sorted(forests)
+    results = []
+    with srv:
+        # warm every forest once
+        for k in keys:
+            srv.submit(k, pools[k][:64]).wait(60)
+        for rate in (2000, 5000, 10000, 20000):
+            reqs = []
+            t_end = time.perf_counter() + args.serve_seconds
+            t_next = time.perf_counter()
+            n_rows = 0
+            while True:
+                t_next += rng.exponential(1.0 / rate)
+                if t_next > t_end:
+                    break
+                while True:
+                    dt = t_next - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(min(dt, 0.001) if dt > 0.0002 else 0)
+                k = keys[rng.integers(len(keys))]
+                m = int(np.clip(round(rng.lognormal(math.log(32), 1.5)), 1, 4096))
+                s = int(rng.integers(0, pools[k].shape[0] - m))
+                reqs.append(srv.submit(k, pools[k][s: s + m]))
+                n_rows += m
+            t0 = time.perf_counter()
+            for r in reqs:
+                r.wait(120)
+            wall = args.serve_seconds + (time.perf_counter() - t0)
+            lat = latency_summary(reqs)
+            results.append({"rate_rps": rate, "requests": len(reqs), "rows": n_rows, "obs_per_s": n_rows / wall,
+                            "achieved_rps": len(reqs) / wall, **lat,
+                            "errors": sum(1 for r in reqs if r.error is not None)})
+    if rank != 0:
+        return
+    best = max(results, key=lambda r: r["obs_per_s"])
+    out = base_line(args, ws, best["obs_per_s"] * ws, 1e3 * args.serve_seconds,
+                    {"workload": "serving", "desc": WORKLOADS["serving"]["desc"], "slots": srv.slots,
+                     "parallelism": f"replicas x{ws}", "l2": "not applicable (request stream)"})
+    out.update({"serving": results, "launches": srv.launches, "gpu_launches": srv.launches,
+                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "e2e": None, "roofline": None,
+                "cpu_baseline": None})
+    print(json.dumps(out))
 
 
 def main():
@@ -333,6 +526,10 @@ def main():
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batched":
+        run_batched(args, ws, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     else:
         run_packed(args, ws, rank, local)
     if ws > 1:

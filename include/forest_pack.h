@@ -220,6 +220,14 @@ void fp_release(fp_device_forest *forest);     /* NULL is a no-op; synchronises 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *fp_last_error(void);
 
+/* Measurement helper, no counterpart in the paper: time `iters` passes of
+ * 16-byte reads over a device buffer of `bytes` (16-byte aligned; pick a size
+ * that stays resident in L2) after one warming pass, and return the
+ * milliseconds in *out_ms; bytes * iters / ms is the L2 read bandwidth used
+ * as the traversal kernel's roofline.  Synchronises `stream`.
+ * Errors: FP_EINVAL, FP_ECUDA. */
+int fp_l2_read_probe(const void *buf, int64_t bytes, int32_t iters, void *stream, float *out_ms);
+
 /* ------------------------------------------------------------------------
  * Plain baseline: the breadth-first per-tree layout the paper measures its
  * layouts against (Section III-A, BF; Section IV-B uses BF as the baseline),

@@ -70,7 +70,7 @@ class fp_batch(ctypes.Structure):
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
-           "fp_plain_release"]
+           "fp_plain_release", "fp_l2_read_probe"]
 
 _lib = None
 _lock = threading.Lock()
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
                 "fp_plain_predict": ([P, P, i64, i32, P, P, P], ctypes.c_int),
                 "fp_plain_bytes": ([P], i64),
                 "fp_plain_release": ([P], None),
+                "fp_l2_read_probe": ([P, i64, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -368,6 +369,16 @@ class PlainForest:
             self.release()
         except Exception:
             pass
+
+
+def fp_l2_read_probe(nbytes: int = 64 << 20, iters: int = 50, stream=None) -> float:
+    """L2 read bandwidth in GB/s over an L2-resident buffer (fp_l2_read_probe)."""
+    T = _torch()
+    buf = T.zeros(nbytes // 4, dtype=T.int32, device="cuda")
+    ms = ctypes.c_float(0.0)
+    _check(lib().fp_l2_read_probe(buf.data_ptr(), buf.numel() * 4, iters, _stream_ptr(stream), ctypes.byref(ms)),
+           "fp_l2_read_probe")
+    return buf.numel() * 4 * iters / (ms.value / 1e3) / 1e9
 
 
 def fp_plain_build(forest, stream=None) -> PlainForest:

@@ -1,0 +1,161 @@
+"""Autotuner for the packed layout and the traversal launch.
+
+Searches the paper's two layout parameters -- stripe width B (trees per bin)
+and interleaved depth d (Section III-A; Fig. 2 sweeps the same pair) -- and
+the launch parameters of the traversal kernel (observations per tile, warps
+per CTA, ring refill level) by timing fp_predict on a sample of the caller's
+observations.  Results are cached per (forest, device, sample size) in a JSON
+file, so a resident forest is tuned once.  All timing runs through the C ABI.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import FPError, fp_pack_forest, fp_predict, fp_upload
+
+_BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
+
+
+def block_bytes(bin_size: int, depth: int) -> int:
+    """Size of a bin's interleaved block when every tree fills its head."""
+    stride = bin_size | 1
+    k = (1 << (depth + 1)) - 1
+    return stride * k * 8 + stride * (k + 1) * 4
+
+
+def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int = 10) -> list[tuple[int, int]]:
+    """(B, d) pairs to try: for each bin size, the deepest head whose block
+    fits the limit and one two levels shallower."""
+    out = []
+    for B in (1, 2, 3, 5, 8, 16, 32, 64, 128):
+        if B > n_trees and out:
+            break
+        B = min(B, n_trees)
+        dmax = max(d for d in range(10) if block_bytes(B, d) <= limit or d == 0)
+        for d in sorted({dmax, max(0, dmax - 2)}, reverse=True):
+            if (B, d) not in out:
+                out.append((B, d))
+    # spread the picks over bin sizes when trimming
+    if len(out) > max_layouts:
+        idx = np.linspace(0, len(out) - 1, max_layouts).round().astype(int)
+        out = [out[i] for i in sorted(set(idx))]
+    return out
+
+
+def candidate_launches(default_tile: int) -> list[tuple[int, int, int]]:
+    """(obs_tile, warps_per_cta, refill_lanes) triples."""
+    tiles = sorted({default_tile, max(32, default_tile // 2 // 32 * 32)}, reverse=True)
+    return [(t, w, r) for t in tiles for w in (32, 16) for r in (32, 16)]
+
+
+def forest_key(forest) -> str:
+    h = hashlib.sha1()
+    for name in ("node_begin", "left", "right", "feature", "threshold", "leaf_class", "cardinality"):
+        a = getattr(forest, name, None)
+        if a is None:
+            continue
+        a = np.ascontiguousarray(a)
+        h.update(name.encode())
+        h.update(np.int64(a.size).tobytes())
+        step = max(1, a.size // 65536)  # a sample of the arrays keeps hashing cheap
+        h.update(a[::step].tobytes())
+    return h.hexdigest()[:16]
+
+
+def _cache_path() -> str:
+    root = os.environ.get("FP_CACHE_DIR") or os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                          ".fpcache")
+    os.makedirs(root, exist_ok=True)
+    return os.path.join(root, "autotune.json")
+
+
+def _time_predict(df, X, votes, cls, reps: int) -> float:
+    import torch
+    fp_predict(df, X, None, cls)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fp_predict(df, X, None, cls)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: bool = True,
+             verbose: bool = False) -> dict:
+    """Time every (layout, launch) candidate on the device rows X (a CUDA
+    float32 tensor [n][n_features]) and return the fastest as a dict of
+    fp_pack_forest keyword arguments plus "ms" and the full "table"."""
+    import torch
+    key = f"{forest_key(forest)}:{torch.cuda.get_device_name()}:{X.shape[0]}"
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return cache[key]
+    layouts = layouts or candidate_layouts(forest.n_trees)
+    cls = torch.empty((X.shape[0],), dtype=torch.int32, device=X.device)
+    table = []
+    ref = None
+    for B, d in layouts:
+        t0 = time.perf_counter()
+        try:
+            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d))
+        except FPError as e:
+            table.append(dict(bin_size=B, interleave_depth=d, error=str(e)))
+            continue
+        pack_s = time.perf_counter() - t0
+        for tile, warps, refill in (launches or candidate_launches(df.info["obs_tile"])):
+            try:
+                df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill)
+            except FPError as e:
+                table.append(dict(bin_size=B, interleave_depth=d, obs_tile=tile, warps_per_cta=warps,
+                                  refill_lanes=refill, error=str(e)))
+                continue
+            ms = _time_predict(df, X, None, cls, reps)
+            if ref is None:
+                ref = cls.clone()
+            same = bool(torch.equal(ref, cls))
+            row = dict(bin_size=B, interleave_depth=d, obs_tile=df.info["obs_tile"], warps_per_cta=warps,
+                       refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)
+            table.append(row)
+            if verbose:
+                print(json.dumps(row), flush=True)
+        df.release()
+    timed = [r for r in table if "ms" in r]
+    if not timed:
+        raise RuntimeError("autotune: no candidate could run")
+    if not all(r["same_classes"] for r in timed):
+        raise RuntimeError("autotune: candidates disagree on classes")
+    best = min(timed, key=lambda r: r["ms"])
+    result = {k: best[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+    result["ms"] = best["ms"]
+    result["rows"] = int(X.shape[0])
+    result["table"] = table
+    if use_cache:
+        cache[key] = result
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f)
+        os.replace(tmp, path)
+    return result
+
+
+def upload_tuned(forest, X, **kw):
+    """Autotune on X, then pack, upload and configure the forest with the best
+    parameters.  Returns (DeviceForest, tuning result)."""
+    best = autotune(forest, X, **kw)
+    df = fp_upload(fp_pack_forest(forest, bin_size=best["bin_size"], interleave_depth=best["interleave_depth"]))
+    df.configure(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"], refill_lanes=best["refill_lanes"])
+    return df, best

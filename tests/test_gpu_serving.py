@@ -1,0 +1,107 @@
+"""The continuous-batching server: requests of different forests and sizes,
+arriving from several threads while launches are in flight, each get exactly
+the answer they get alone (and the oracle's)."""
+import threading
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from paper_1806_07300_gb300.serving import ForestServer, latency_summary
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(scope="module")
+def served():
+    tiny = datagen.forest("tiny")
+    b0 = datagen.forest("batched0")
+    b2 = datagen.forest("batched2")
+    rows = {"tiny": datagen.test_rows("tiny")[0], "b0": datagen.test_rows("batched0", 20000)[0],
+            "b2": datagen.test_rows("batched2", 20000)[0]}
+    return {"tiny": tiny, "b0": b0, "b2": b2}, rows
+
+
+def _server(forests, **kw):
+    srv = ForestServer(**kw)
+    for name, f in forests.items():
+        srv.add_forest(name, f, pass_bytes=(4096 if name == "b2" else 0))
+    return srv
+
+
+def _requests(rows, n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    names = sorted(rows)
+    for _ in range(n):
+        name = names[rng.integers(len(names))]
+        m = int(np.clip(round(rng.lognormal(np.log(32), 1.5)), 1, 4096))
+        start = int(rng.integers(0, rows[name].shape[0] - m))
+        out.append((name, rows[name][start: start + m]))
+    return out
+
+
+def test_mix_equals_alone_and_oracle(served):
+    forests, rows = served
+    reqs = _requests(rows, 300, seed=3)
+    with _server(forests, slots=3, max_rows=20000, return_votes=True) as srv:
+        handles = [None] * len(reqs)
+
+        def client(lo, hi):
+            for i in range(lo, hi):
+                handles[i] = srv.submit(*reqs[i])
+
+        ts = [threading.Thread(target=client, args=(k * 100, (k + 1) * 100)) for k in range(3)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        for h in handles:
+            assert h.wait(60) and h.error is None
+        assert srv.launches >= 1
+    # alone: a fresh server, one request at a time
+    with _server(forests, slots=1, return_votes=True) as alone:
+        for (name, X), h in zip(reqs[:60], handles[:60]):
+            a = alone.submit(name, X)
+            assert a.wait(60) and a.error is None
+            np.testing.assert_array_equal(a.classes, h.classes)
+            np.testing.assert_array_equal(a.votes, h.votes)
+    for (name, X), h in zip(reqs, handles):
+        ref = oracle.predict(forests[name], X, leaves=False)
+        np.testing.assert_array_equal(h.classes, ref["cls"])
+        np.testing.assert_array_equal(h.votes.astype(np.uint32), ref["votes"])
+    s = latency_summary(handles)
+    assert s["n"] == len(reqs) and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_admission_waits_for_memory(served):
+    """With free memory reported too small, launches wait for those in
+    flight to finish instead of starting; every request still completes."""
+    forests, rows = served
+    reqs = _requests(rows, 60, seed=5)
+    srv = _server(forests, slots=2, max_rows=2000)
+    real = torch.cuda.mem_get_info
+    calls = {"n": 0}
+
+    def tight(device=None):
+        calls["n"] += 1
+        free, total = real(device)
+        return (srv.mem_margin - 1, total) if calls["n"] % 2 else (free, total)
+
+    srv._admit_info = tight
+    with srv:
+        hs = [srv.submit(*r) for r in reqs]
+        for h in hs:
+            assert h.wait(60) and h.error is None
+    assert srv.rejected_for_memory > 0
+    for (name, X), h in zip(reqs, hs):
+        np.testing.assert_array_equal(h.classes, oracle.predict(forests[name], X, leaves=False)["cls"])
