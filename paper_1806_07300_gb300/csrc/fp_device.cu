@@ -73,13 +73,20 @@ size_t smem_bytes(int R, int F, int head_smem, int C, int warps, bool leaves) {
     return xs + FP_NBUF * (size_t)head_smem + votes + (size_t)warps * FP_RING * 8;
 }
 
+// The kernel variant for a block size: up to 512 threads run the three-CTAs-
+// per-SM build (<= 42 registers), larger blocks the one-CTA build.
+template <bool LEAVES>
+void (*traverse_kernel(int threads))(TravParams) {
+    return threads <= 512 ? fp_traverse_kernel<LEAVES, 3> : fp_traverse_kernel<LEAVES, 1>;
+}
+
 template <bool LEAVES>
 int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
-    cudaError_t e = cudaFuncSetAttribute(fp_traverse_kernel<LEAVES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = traverse_kernel<LEAVES>(f->threads);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_traverse_kernel<LEAVES>, f->threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, f->threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) {
         fp_set_error("traversal kernel does not fit on an SM (%zu bytes of shared memory)", smem);
@@ -274,7 +281,7 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    fp_traverse_kernel<false><<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<false>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (scratch) cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
@@ -354,7 +361,7 @@ extern "C" int fp_predict_noalloc(const fp_device_forest *f, const float *X, int
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    fp_traverse_kernel<false><<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<false>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
     return FP_OK;
@@ -375,7 +382,7 @@ extern "C" int fp_predict_leaves(const fp_device_forest *f, const float *X, int6
     p.n_items = p.n_tiles * f->hdr.n_passes;
     p.out_leaf = out_leaf;
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_leaves);
-    fp_traverse_kernel<true><<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
+    traverse_kernel<true>(f->threads)<<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<leaves> launch");
     return FP_OK;

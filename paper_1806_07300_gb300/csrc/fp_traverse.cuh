@@ -90,10 +90,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // One super-node: a single 256-bit load (32-byte aligned, one L2 sector).
+// The memory clobber keeps the load where it is written, ahead of the work
+// meant to overlap its latency.
 __device__ __forceinline__ void ld_super(const FpSuper *p, uint32_t w[8]) {
     asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                  : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
-                 : "l"(p));
+                 : "l"(p)
+                 : "memory");
 }
 
 __device__ __forceinline__ void report(int32_t *status, int32_t code) { atomicCAS(status, 0, code); }
@@ -172,12 +175,14 @@ __device__ __forceinline__ void pop_tasks(const TravParams &p, const uint2 *ring
     head += npop;
 }
 
-// One deep step: two levels of the tree per 32-byte load.
+// One deep step, two levels of the tree per 32-byte load, in two halves: the
+// load is issued first and consumed after the warp has done other work (a
+// head burst), so the L2 latency overlaps that work.
+__device__ __forceinline__ void deep_issue(const LaneTask &L, uint32_t w[8]) { ld_super(L.tb + L.ref, w); }
+
 template <bool LEAVES>
-__device__ __forceinline__ void deep_step(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
-                                          LaneTask &L) {
-    uint32_t w[8];
-    ld_super(L.tb + L.ref, w);
+__device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
+                                            LaneTask &L, const uint32_t w[8]) {
     const int R = p.R;
     const float x0 = xs[(w[3] & 1023u) * R + L.r];
     const uint32_t d0 = x0 <= __uint_as_float(w[0]) ? 0u : 1u;
@@ -191,7 +196,7 @@ __device__ __forceinline__ void deep_step(const TravParams &p, const float *xs, 
         int32_t leaf_id = -1;
         if (LEAVES) leaf_id = p.deep_leaf[4 * ((int64_t)(L.tb - p.deep) + L.ref) + 2 * d0 + d1];
         finish<LEAVES>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
-    } else if (++L.steps < (1u << 24)) {  // a path is shorter than any tree
+    } else if (nref > L.ref) {  // super-nodes only point forward, so every walk ends
         L.ref = nref;
     } else {
         report(p.status, FP_ERR_FLAG_DEVICE);
@@ -265,6 +270,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
     const FpPass ps = p.passes[pass];
     const int nbins = ps.bin_end - ps.bin_begin;
+    const float inv_rows = 1.0f / (float)rows;
 
     // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
     {
@@ -320,34 +326,45 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         const uint8_t *blk = hbuf0 + buf * p.head_smem;
         const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
         const uint32_t *hexit = reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * 8);
-        volatile int *next = &sh.task_next[buf];
 
         for (;;) {
-            if (*next >= ntask) break;  // the bin's tasks are all claimed
+            uint32_t w[8];
+            if (L.active) deep_issue(L, w);  // in flight during the burst below
             if (tail - head <= p.refill) {
                 // burst: 32 consecutive tasks through the head, all lanes together
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&sh.task_next[buf], 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= ntask) break;
+                if (base >= ntask) break;  // the bin is claimed out; the step above is issued again later
                 const bool my = lane < ntask - base;
                 const int task = base + lane;
-                const int k2 = my ? task / rows : 0;
+                // task / rows by a float reciprocal, corrected to the exact quotient
+                int k2 = my ? (int)((float)task * inv_rows) : 0;
+                if (my) {
+                    k2 -= k2 * rows > task;
+                    k2 += (k2 + 1) * rows <= task;
+                }
                 const int r2 = my ? task - k2 * rows : 0;
                 uint32_t hr = 0;  // head rank, then nranks + exit index
                 bool busy = my;
-                int guard = 0;
+                const uint2 *hn = hnode + k2;  // this lane's tree column of the block
+                const float *xr = xs + r2;     // this lane's row
                 while (__any_sync(0xffffffffu, busy)) {
-                    if (busy) {
-                        const uint2 nd = hnode[hr * stride + k2];
-                        const uint32_t m = nd.y;
-                        hr = xs[(m >> 22) * R + r2] <= __uint_as_float(nd.x) ? (m & FP_TARGET_MASK)
-                                                                               : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
-                        busy = hr < (uint32_t)nranks;
-                        if (++guard > nranks && busy) {  // a path visits each rank at most once
-                            report(p.status, FP_ERR_FLAG_DEVICE);
-                            busy = false;
-                            hr = (uint32_t)(nranks + nexits);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {  // two steps per vote
+                        if (busy) {
+                            const uint2 nd = hn[hr * stride];
+                            const uint32_t m = nd.y;
+                            uint32_t nh = xr[(m >> 22) * R] <= __uint_as_float(nd.x)
+                                              ? (m & FP_TARGET_MASK)
+                                              : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
+                            busy = nh < (uint32_t)nranks;
+                            if (busy && nh <= hr) {  // ranks grow along every path of a valid block
+                                report(p.status, FP_ERR_FLAG_DEVICE);
+                                busy = false;
+                                nh = (uint32_t)(nranks + nexits);
+                            }
+                            hr = nh;
                         }
                     }
                 }
@@ -367,8 +384,8 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 tail += __popc(pm);
                 __syncwarp();
             }
+            if (L.active) deep_finish<LEAVES>(p, xs, svotes, row0, L, w);
             pop_tasks(p, ring, head, tail, L, lt_mask);
-            if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
         }
         // this warp reads the bin's block no more; the last warp refills the buffer
         __syncwarp();
@@ -386,7 +403,11 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         __syncwarp();
         pop_tasks(p, ring, head, tail, L, lt_mask);
         if (!__any_sync(0xffffffffu, L.active)) break;
-        if (L.active) deep_step<LEAVES>(p, xs, svotes, row0, L);
+        if (L.active) {
+            uint32_t w[8];
+            deep_issue(L, w);
+            deep_finish<LEAVES>(p, xs, svotes, row0, L, w);
+        }
     }
     __syncthreads();
 
@@ -438,8 +459,11 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 
 }
 
-template <bool LEAVES>
-__global__ void __launch_bounds__(1024, 1) fp_traverse_kernel(const TravParams p) {
+// MINB = 1: one CTA of up to 1024 threads per SM (up to 64 registers a thread);
+// MINB = 3: up to three CTAs of up to 512 threads (at most 42 registers), for
+// launches whose shared memory leaves room for three CTAs.
+template <bool LEAVES, int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? 1024 : 512, MINB) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
