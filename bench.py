@@ -13,7 +13,11 @@ Workloads (--workload):
   batched  8 forests (32..512 trees) and uneven batches (1..100,000 rows) in
            one persistent launch replayed from a CUDA graph;
   serving  4 resident forests behind the continuous-batching server, Poisson
-           arrivals at 2k/5k/10k/20k requests/s; p50/p99 latency.
+           arrivals at 2k/5k/10k/20k requests/s; p50/p99 latency;
+  ablation the layout ablation on the HBM-resident forest (the GPU counterpart
+           of the paper's Figs. 4 and 6): plain BF, DF order, Stat, Stat from
+           statistics counted on observations, Bin with levels 0..d, Bin with
+           the most visited nodes, and the autotuned layout.
 
 Prints one JSON line (rank 0).  Besides the headline value it reports the
 plain breadth-first GPU baseline on the same inputs (the faster of its two
@@ -22,7 +26,7 @@ the traversal kernel against the measured HBM copy bandwidth and a measured
 L2 read bandwidth, and the CPU oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl packed|reference]
-                    [--workload hbm|image|tiny|batched|serving] [--rows N]
+                    [--workload hbm|image|tiny|batched|serving|ablation] [--rows N]
 """
 from __future__ import annotations
 
@@ -52,6 +56,7 @@ WORKLOADS = {
                                  "one persistent launch replayed from a CUDA graph"),
     "serving": dict(rows=0, desc="4 resident forests (tiny, image, hbm, 64-tree 50-class 100-feature), Poisson "
                                  "arrivals, rows/request LogNormal(ln 32, 1.5) clipped to [1, 4096]"),
+    "ablation": dict(rows=4_000_000, desc="layout ablation on the HBM-resident forest (256 trees, 4,000,000 rows)"),
 }
 
 # Layout and launch candidates timed by the autotuner for the default workload
@@ -67,6 +72,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="packed", choices=["packed", "reference"])
     ap.add_argument("--workload", default="hbm", choices=sorted(WORKLOADS))
+    ap.add_argument("--forest", default="hbm", help="forest of the ablation workload")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--no-plain", action="store_true")
@@ -521,6 +527,87 @@ def run_serving(args, ws, rank, local):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------- ablation
+
+def run_ablation(args, ws, rank, local):
+    """Each layout variant timed on the same rows; classes compared with the
+    plain baseline's."""
+    import torch
+    import datagen
+    import paper_1806_07300_gb300 as fp
+    from paper_1806_07300_gb300 import autotune as at
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = args.forest
+    n = args.rows or WORKLOADS["ablation"]["rows"]
+    forest = datagen.forest(name)
+    Xh, _ = datagen.test_rows(name, n)
+    X = torch.from_numpy(Xh).to(dev)
+    C = forest.n_classes
+    cls = torch.empty((n,), dtype=torch.int32, device=dev)
+    reps = max(2, args.steps // 4)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    pf = fp.fp_plain_build(forest)
+    pv = torch.empty((n, C), dtype=torch.int32, device=dev)
+    ref = torch.empty((n,), dtype=torch.int32, device=dev)
+    for order, oname in ((fp.FP_PLAIN_OBS_FASTEST, "obs_fastest"), (fp.FP_PLAIN_TREE_FASTEST, "tree_fastest")):
+        ms = timed(lambda: fp.fp_plain_predict(pf, X, order, pv, ref))
+        rows.append({"layout": f"BF plain ({oname})", "ms": ms})
+    pf.release()
+    del pv
+    sample = X[: min(n, 200_000)]
+    inferred = datagen.Forest(forest.n_features, forest.n_classes, forest.node_begin, forest.left, forest.right,
+                              forest.feature, forest.threshold, forest.leaf_class, fp.infer_cardinality(forest, sample))
+    no_stats = datagen.Forest(forest.n_features, forest.n_classes, forest.node_begin, forest.left, forest.right,
+                              forest.feature, forest.threshold, forest.leaf_class, forest.cardinality)
+    no_stats.cardinality = None  # packed without statistics: children keep left-first order
+    best = at.autotune(forest, X[: min(n, 1 << 20)], layouts=HBM_LAYOUTS if name == "hbm" else None,
+                       launches=HBM_LAUNCHES if name == "hbm" else None)
+    variants = [
+        ("DF order, roots only (no statistics)", no_stats, dict(bin_size=1, interleave_depth=0), {}),
+        ("Stat (training cardinalities), roots only", forest, dict(bin_size=1, interleave_depth=0), {}),
+        ("Stat (counted on 200k observations), roots only", inferred, dict(bin_size=1, interleave_depth=0), {}),
+        ("Bin B=16, levels 0..4", forest, dict(bin_size=16, interleave_depth=4, head_select=1), {}),
+        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4), {}),
+        ("autotuned", forest, dict(bin_size=best["bin_size"], interleave_depth=best["interleave_depth"]),
+         dict(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"], refill_lanes=best["refill_lanes"])),
+    ]
+    for label, f, params, launch in variants:
+        df = fp.fp_upload(fp.fp_pack_forest(f, **params))
+        if launch:
+            df.configure(**launch)
+        ms = timed(lambda: fp.fp_predict(df, X, None, cls))
+        rows.append({"layout": label, **params, **launch, "passes": df.info["passes"], "ms": ms,
+                     "same_classes": bool(torch.equal(cls, ref))})
+        df.release()
+    plain_best = min(r["ms"] for r in rows[:2])
+    for r in rows:
+        r["obs_per_s"] = n / (r["ms"] / 1e3)
+        r["vs_plain"] = plain_best / r["ms"]
+    if rank != 0:
+        return
+    top = min(rows[2:], key=lambda r: r["ms"])
+    out = base_line(args, ws, ws * top["obs_per_s"], top["ms"] * args.steps,
+                    {"workload": "ablation", "forest": name, "rows": n, "parallelism": f"replicas x{ws}",
+                     "l2": "inputs larger than L2; no flush"})
+    out.update({"ablation": rows, "e2e": None, "roofline": None, "cpu_baseline": None,
+                "gpu_launches": len(rows) * (reps + 1)})
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -530,6 +617,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload == "serving":
         run_serving(args, ws, rank, local)
+    elif args.workload == "ablation":
+        run_ablation(args, ws, rank, local)
     else:
         run_packed(args, ws, rank, local)
     if ws > 1:

@@ -220,6 +220,22 @@ void fp_release(fp_device_forest *forest);     /* NULL is a no-op; synchronises 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *fp_last_error(void);
 
+/* Statistics inferred from observations (Section III-A: leaf cardinalities
+ * "can also be inferred after training using a suitably large set of
+ * observations").  For the leaf ids that fp_predict_leaves wrote for n
+ * observations, add 1 to leaf_count[node_begin[t] + out_leaf[i][t]] for every
+ * (i, t).  Summing each leaf's count into its ancestors gives cardinalities to
+ * pack the forest with.
+ *   out_leaf    device, [n][n_trees] int32 tree-local leaf ids
+ *   node_begin  device, [n_trees+1] int64 offsets of the forest's node arrays
+ *   leaf_count  device, int64 per node of the forest; zeroed by the caller,
+ *               accumulated (so several samples can be added up)
+ *   status      device int32, set to FP_EDEVICE if a leaf id is not a node of
+ *               its tree (that entry is skipped)
+ * Asynchronous on stream.  Errors: FP_EINVAL, FP_ECUDA. */
+int fp_count_leaves(const int32_t *out_leaf, int64_t n, int32_t n_trees, const int64_t *node_begin,
+                    int64_t *leaf_count, int32_t *status, void *stream);
+
 /* Measurement helper, no counterpart in the paper: time `iters` passes of
  * 16-byte reads over a device buffer of `bytes` (16-byte aligned; pick a size
  * that stays resident in L2) after one warming pass, and return the

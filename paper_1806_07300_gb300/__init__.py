@@ -70,7 +70,7 @@ class fp_batch(ctypes.Structure):
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
-           "fp_plain_release", "fp_l2_read_probe"]
+           "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves"]
 
 _lib = None
 _lock = threading.Lock()
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
                 "fp_plain_bytes": ([P], i64),
                 "fp_plain_release": ([P], None),
                 "fp_l2_read_probe": ([P, i64, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+                "fp_count_leaves": ([P, i64, i32, P, P, P, P], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -379,6 +380,59 @@ def fp_l2_read_probe(nbytes: int = 64 << 20, iters: int = 50, stream=None) -> fl
     _check(lib().fp_l2_read_probe(buf.data_ptr(), buf.numel() * 4, iters, _stream_ptr(stream), ctypes.byref(ms)),
            "fp_l2_read_probe")
     return buf.numel() * 4 * iters / (ms.value / 1e3) / 1e9
+
+
+def fp_count_leaves(out_leaf, node_begin, leaf_count, status, stream=None) -> None:
+    """Add the leaves reached in out_leaf ([n][T] int32, device) to leaf_count
+    (int64 per node, device); node_begin is the forest's [T+1] offsets (device)."""
+    T = _torch()
+    n, nt = out_leaf.shape
+    lp = _dptr(out_leaf, T.int32, None, "out_leaf")
+    nb = _dptr(node_begin, T.int64, (nt + 1,), "node_begin")
+    cp = _dptr(leaf_count, T.int64, None, "leaf_count")
+    sp = _dptr(status, T.int32, None, "status")
+    _check(lib().fp_count_leaves(lp, n, nt, nb, cp, sp, _stream_ptr(stream)), "fp_count_leaves")
+
+
+def infer_cardinality(forest, X, device_forest=None, stream=None):
+    """Cardinalities of every node of `forest` counted from the observations
+    X (CUDA float32 [n][n_features]): the leaves reached on the device
+    (fp_predict_leaves, fp_count_leaves), then each internal node the sum of
+    its children.  Returns an int64 numpy array aligned with the node arrays."""
+    T = _torch()
+    df = device_forest or fp_upload(fp_pack_forest(forest), stream)
+    leaves = df.predict_leaves(X, stream)
+    dev = X.device
+    nb = T.from_numpy(np.ascontiguousarray(forest.node_begin, dtype=np.int64)).to(dev)
+    counts = T.zeros(forest.n_nodes, dtype=T.int64, device=dev)
+    status = T.zeros(1, dtype=T.int32, device=dev)
+    fp_count_leaves(leaves, nb, counts, status, stream)
+    T.cuda.synchronize()
+    if int(status.item()) != FP_OK:
+        raise FPError(FP_EDEVICE, "fp_count_leaves: a leaf id was not a node of its tree")
+    card = counts.cpu().numpy()
+    left, right = np.asarray(forest.left), np.asarray(forest.right)
+    for t in range(forest.n_trees):
+        b, e = int(forest.node_begin[t]), int(forest.node_begin[t + 1])
+        # children before parents (post-order), whatever the node numbering
+        order = _postorder(left[b:e], right[b:e])
+        for v in order:
+            if left[b + v] >= 0:
+                card[b + v] = card[b + left[b + v]] + card[b + right[b + v]]
+    return card
+
+
+def _postorder(left, right):
+    out, stack = [], [(0, False)]
+    while stack:
+        v, done = stack.pop()
+        if done or left[v] < 0:
+            out.append(v)
+            continue
+        stack.append((v, True))
+        stack.append((int(right[v]), False))
+        stack.append((int(left[v]), False))
+    return out
 
 
 def fp_plain_build(forest, stream=None) -> PlainForest:
