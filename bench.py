@@ -61,8 +61,8 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-HBM_LAYOUTS = [(3, 8), (2, 8), (1, 9), (16, 4), (64, 2)]
-HBM_LAUNCHES = [(768, 32, 32), (1024, 32, 16)]
+HBM_LAYOUTS = [(3, 8, 1), (2, 9, 1), (1, 10, 1), (16, 5, 1), (3, 8, 0)]  # (B, d, head_select)
+HBM_LAUNCHES = [(768, 32, 16), (1024, 32, 16)]
 
 
 def parse():
@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--bin-size", type=int, default=0)
     ap.add_argument("--depth", type=int, default=-1)
+    ap.add_argument("--head-select", type=int, default=1, help="1: levels 0..d (implicit slots); 0: ranked")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
@@ -249,7 +250,8 @@ def tuned_forest(args, forest, X, name):
     explicit = args.bin_size or args.depth >= 0 or args.tile or args.warps or args.refill
     tuning = None
     if explicit or args.no_autotune:
-        params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes)
+        params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes,
+                      head_select=args.head_select)
         df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
         df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill)
     else:
@@ -257,12 +259,10 @@ def tuned_forest(args, forest, X, name):
         layouts = HBM_LAYOUTS if name == "hbm" else None
         launches = HBM_LAUNCHES if name == "hbm" else None
         best = at.autotune(forest, sample, layouts=layouts, launches=launches)
-        tuning = {k: best[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+        tuning = {k: best[k] for k in at.LAYOUT_KEYS + at.LAUNCH_KEYS}
         tuning["candidates"] = len([r for r in best["table"] if "ms" in r])
-        df = fp.fp_upload(fp.fp_pack_forest(forest, bin_size=best["bin_size"],
-                                            interleave_depth=best["interleave_depth"]))
-        df.configure(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"],
-                     refill_lanes=best["refill_lanes"])
+        df = fp.fp_upload(fp.fp_pack_forest(forest, **{k: best[k] for k in at.LAYOUT_KEYS}))
+        df.configure(**{k: best[k] for k in at.LAUNCH_KEYS})
     return df, tuning
 
 
@@ -378,7 +378,8 @@ def run_packed(args, ws, rank, local):
     avg_launch_ms = statistics.mean(per_launch_ms)
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    params = {k: info[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+    params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "obs_tile", "warps_per_cta",
+                                   "refill_lanes")}
     traffic = profiled_traffic(name, params, n)
     out = base_line(args, ws, value, total_ms,
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
@@ -581,9 +582,10 @@ def run_ablation(args, ws, rank, local):
         ("Stat (training cardinalities), roots only", forest, dict(bin_size=1, interleave_depth=0), {}),
         ("Stat (counted on 200k observations), roots only", inferred, dict(bin_size=1, interleave_depth=0), {}),
         ("Bin B=16, levels 0..4", forest, dict(bin_size=16, interleave_depth=4, head_select=1), {}),
-        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4), {}),
-        ("autotuned", forest, dict(bin_size=best["bin_size"], interleave_depth=best["interleave_depth"]),
-         dict(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"], refill_lanes=best["refill_lanes"])),
+        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4, head_select=0), {}),
+        ("Bin B=3, levels 0..8", forest, dict(bin_size=3, interleave_depth=8, head_select=1), {}),
+        ("Bin B=3, 511 most visited nodes", forest, dict(bin_size=3, interleave_depth=8, head_select=0), {}),
+        ("autotuned", forest, {k: best[k] for k in at.LAYOUT_KEYS}, {k: best[k] for k in at.LAUNCH_KEYS}),
     ]
     for label, f, params, launch in variants:
         df = fp.fp_upload(fp.fp_pack_forest(f, **params))

@@ -2,8 +2,8 @@
  * datagen.c -- seeded synthetic inputs for forest classification.
  *
  * This module produces the two inputs of the classification path that the
- * paper takes as given (Section III: "the input to this process is a trained
- * forest"): observation matrices and a trained random forest.  It contains no
+ * paper takes as given (Section III starts from a forest that has already
+ * been trained): observation matrices and a trained random forest.  It contains no
  * part of the packing or classification method itself; both the CPU oracle
  * and the GPU library consume what it writes.
  *

@@ -211,6 +211,28 @@ int fp_predict_batched(const fp_device_forest *const *forests, const fp_batch *b
  * FP_EDEVICE).  Clears the word.  Blocks the calling host thread. */
 int fp_sync_status(const fp_device_forest *forest, void *stream);
 
+/* Fault injection for failure-detection tests (the paper has no counterpart).
+ * Nothing it does faults, traps or hangs a GPU: it makes the library's own
+ * error paths run.
+ *   FP_FAULT_ALLOC           forest ignored (may be NULL); the next `value`
+ *                            device allocations made by fp_upload and by the
+ *                            scratch of fp_predict / fp_predict_batched fail
+ *                            with FP_ENOMEM (0 clears)
+ *   FP_FAULT_WAIT_LIMIT      a bin-block wait of this forest's kernels polls its
+ *                            barrier at most `value` times (1 .. 2^24; the
+ *                            default is 2^24) before recording FP_ETIMEOUT
+ *   FP_FAULT_STALL_BIN_COPY  value 1: this forest's bin-block waits ignore
+ *                            completed copies, so every launch records
+ *                            FP_ETIMEOUT (read by fp_sync_status) and leaves
+ *                            its outputs unspecified; the copies still land
+ *                            before the kernel exits.  value 0 restores.
+ * Not thread-safe against concurrent launches of the same forest.
+ * Errors: FP_EINVAL (unknown kind, value out of range, NULL forest). */
+#define FP_FAULT_ALLOC 1
+#define FP_FAULT_WAIT_LIMIT 2
+#define FP_FAULT_STALL_BIN_COPY 3
+int fp_inject_fault(fp_device_forest *forest, int32_t kind, int64_t value);
+
 /* Sizes of a resident forest (same fields as fp_packed_info_get). */
 int fp_device_info_get(const fp_device_forest *forest, fp_packed_info *info);
 
@@ -220,9 +242,9 @@ void fp_release(fp_device_forest *forest);     /* NULL is a no-op; synchronises 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *fp_last_error(void);
 
-/* Statistics inferred from observations (Section III-A: leaf cardinalities
- * "can also be inferred after training using a suitably large set of
- * observations").  For the leaf ids that fp_predict_leaves wrote for n
+/* Statistics inferred from observations (Section III-A allows the leaf
+ * cardinalities that drive the Stat ordering to be estimated after training
+ * by classifying a large sample of observations).  For the leaf ids that fp_predict_leaves wrote for n
  * observations, add 1 to leaf_count[node_begin[t] + out_leaf[i][t]] for every
  * (i, t).  Summing each leaf's count into its ancestors gives cardinalities to
  * pack the forest with.

@@ -21,7 +21,7 @@
  *                    BF    breadth-first per tree;
  *                    DF    depth-first (pre-order, left first) per tree;
  *                    DF-   DF with leaves replaced by one shared class node
- *                          per class at the end of the tree's array;
+ *                          per class, appended after the tree's internal nodes;
  *                    Stat  DF- where, at each parent, the child of larger
  *                          training cardinality is placed adjacent (left on
  *                          ties) and an internal child is always adjacent when

@@ -70,7 +70,7 @@ class fp_batch(ctypes.Structure):
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
-           "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves"]
+           "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves", "fp_inject_fault"]
 
 _lib = None
 _lock = threading.Lock()
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
                 "fp_plain_release": ([P], None),
                 "fp_l2_read_probe": ([P, i64, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
                 "fp_count_leaves": ([P, i64, i32, P, P, P, P], ctypes.c_int),
+                "fp_inject_fault": ([P, i32, i64], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -247,6 +248,19 @@ def fp_predict_batched(forests, Xs, out_votes=None, out_class=None, stream=None)
 
 def fp_sync_status(forest: "DeviceForest", stream=None) -> int:
     return lib().fp_sync_status(forest.handle, _stream_ptr(stream))
+
+
+FP_FAULT_ALLOC, FP_FAULT_WAIT_LIMIT, FP_FAULT_STALL_BIN_COPY = 1, 2, 3
+
+
+def fp_inject_fault(forest, kind: int, value: int) -> None:
+    """Fault injection for failure-detection tests: FP_FAULT_ALLOC (forest may
+    be None) makes the next `value` device allocations fail with FP_ENOMEM;
+    FP_FAULT_WAIT_LIMIT bounds a bin-block wait to `value` polls;
+    FP_FAULT_STALL_BIN_COPY=1 makes the forest's bin waits run out, so its
+    launches record FP_ETIMEOUT (0 restores)."""
+    handle = forest.handle if forest is not None else None
+    _check(lib().fp_inject_fault(handle, kind, value), "fp_inject_fault")
 
 
 def fp_release(forest: "DeviceForest") -> None:

@@ -1,8 +1,9 @@
 """Autotuner for the packed layout and the traversal launch.
 
 Searches the paper's two layout parameters -- stripe width B (trees per bin)
-and interleaved depth d (Section III-A; Fig. 2 sweeps the same pair) -- and
-the launch parameters of the traversal kernel (observations per tile, warps
+and interleaved depth d (Section III-A; Fig. 2 sweeps the same pair) -- with
+the kind of head (the interleaved levels 0..d, or the most visited nodes),
+and the launch parameters of the traversal kernel (observations per tile, warps
 per CTA, ring refill level) by timing fp_predict on a sample of the caller's
 observations.  Results are cached per (forest, device, sample size) in a JSON
 file, so a resident forest is tuned once.  All timing runs through the C ABI.
@@ -19,6 +20,9 @@ import numpy as np
 from . import FPError, fp_pack_forest, fp_predict, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
+LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select")
+_SEARCH_VERSION = "levels-v5"  # cached results of an older search space are not reused
+LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes")
 
 
 def block_bytes(bin_size: int, depth: int) -> int:
@@ -28,18 +32,19 @@ def block_bytes(bin_size: int, depth: int) -> int:
     return stride * k * 8 + stride * (k + 1) * 4
 
 
-def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int = 10) -> list[tuple[int, int]]:
-    """(B, d) pairs to try: for each bin size, the deepest head whose block
-    fits the limit and one two levels shallower."""
+def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int = 10) -> list[tuple[int, int, int]]:
+    """(B, d, head_select) triples to try: for each bin size, level heads
+    (head_select 1) as deep as the block limit allows and one level
+    shallower, and the ranked head of the deepest fitting d."""
     out = []
     for B in (1, 2, 3, 5, 8, 16, 32, 64, 128):
         if B > n_trees and out:
             break
         B = min(B, n_trees)
-        dmax = max(d for d in range(10) if block_bytes(B, d) <= limit or d == 0)
-        for d in sorted({dmax, max(0, dmax - 2)}, reverse=True):
-            if (B, d) not in out:
-                out.append((B, d))
+        dmax = max(d for d in range(12) if block_bytes(B, d) <= limit or d == 0)
+        for cand in ((B, dmax, 1), (B, max(0, dmax - 1), 1), (B, min(dmax, 9), 0)):
+            if cand not in out:
+                out.append(cand)
     # spread the picks over bin sizes when trimming
     if len(out) > max_layouts:
         idx = np.linspace(0, len(out) - 1, max_layouts).round().astype(int)
@@ -93,7 +98,7 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
     float32 tensor [n][n_features]) and return the fastest as a dict of
     fp_pack_forest keyword arguments plus "ms" and the full "table"."""
     import torch
-    key = f"{forest_key(forest)}:{torch.cuda.get_device_name()}:{X.shape[0]}"
+    key = f"{forest_key(forest)}:{torch.cuda.get_device_name()}:{X.shape[0]}:{_SEARCH_VERSION}"
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -108,26 +113,29 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
     cls = torch.empty((X.shape[0],), dtype=torch.int32, device=X.device)
     table = []
     ref = None
-    for B, d in layouts:
+    for lay in layouts:
+        B, d = lay[0], lay[1]
+        sel = lay[2] if len(lay) > 2 else 0
         t0 = time.perf_counter()
         try:
-            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d))
+            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel))
         except FPError as e:
-            table.append(dict(bin_size=B, interleave_depth=d, error=str(e)))
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, error=str(e)))
             continue
         pack_s = time.perf_counter() - t0
         for tile, warps, refill in (launches or candidate_launches(df.info["obs_tile"])):
             try:
                 df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill)
             except FPError as e:
-                table.append(dict(bin_size=B, interleave_depth=d, obs_tile=tile, warps_per_cta=warps,
-                                  refill_lanes=refill, error=str(e)))
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=tile,
+                                  warps_per_cta=warps, refill_lanes=refill, error=str(e)))
                 continue
             ms = _time_predict(df, X, None, cls, reps)
             if ref is None:
                 ref = cls.clone()
             same = bool(torch.equal(ref, cls))
-            row = dict(bin_size=B, interleave_depth=d, obs_tile=df.info["obs_tile"], warps_per_cta=warps,
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=df.info["obs_tile"],
+                       warps_per_cta=warps,
                        refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)
             table.append(row)
             if verbose:
@@ -139,7 +147,7 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
     if not all(r["same_classes"] for r in timed):
         raise RuntimeError("autotune: candidates disagree on classes")
     best = min(timed, key=lambda r: r["ms"])
-    result = {k: best[k] for k in ("bin_size", "interleave_depth", "obs_tile", "warps_per_cta", "refill_lanes")}
+    result = {k: best[k] for k in LAYOUT_KEYS + LAUNCH_KEYS}
     result["ms"] = best["ms"]
     result["rows"] = int(X.shape[0])
     result["table"] = table
@@ -156,6 +164,6 @@ def upload_tuned(forest, X, **kw):
     """Autotune on X, then pack, upload and configure the forest with the best
     parameters.  Returns (DeviceForest, tuning result)."""
     best = autotune(forest, X, **kw)
-    df = fp_upload(fp_pack_forest(forest, bin_size=best["bin_size"], interleave_depth=best["interleave_depth"]))
-    df.configure(obs_tile=best["obs_tile"], warps_per_cta=best["warps_per_cta"], refill_lanes=best["refill_lanes"])
+    df = fp_upload(fp_pack_forest(forest, **{k: best[k] for k in LAYOUT_KEYS}))
+    df.configure(**{k: best[k] for k in LAUNCH_KEYS})
     return df, best

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -32,12 +33,25 @@ struct fp_device_forest {
     int32_t head_smem = 0;
     size_t smem_votes = 0, smem_leaves = 0;
     int32_t grid_votes = 0, grid_leaves = 0;  // resident CTAs for a persistent launch
+    int32_t spin_limit = FP_SPIN_LIMIT;       // fault injection may lower it
+    int32_t stall = 0;                        // fault injection: bin waits run out
 };
 
 namespace {
 
 std::mutex g_pool_mu;
 std::vector<int> g_pool_ready;
+std::atomic<int64_t> g_fail_allocs{0};  // fault injection: device allocations still to fail
+
+// true when fault injection takes this allocation
+bool injected_alloc_failure(const char *what) {
+    int64_t k = g_fail_allocs.load();
+    while (k > 0 && !g_fail_allocs.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k <= 0) return false;
+    fp_set_error("%s: injected allocation failure", what);
+    return true;
+}
 
 int cuda_fail(cudaError_t e, const char *what) {
     fp_set_error("%s: %s", what, cudaGetErrorString(e));
@@ -61,6 +75,7 @@ int scratch_alloc(int device, void **out, size_t bytes, cudaStream_t s) {
             g_pool_ready[device] = 1;
         }
     }
+    if (injected_alloc_failure("cudaMallocAsync(scratch)")) return FP_ENOMEM;
     cudaError_t e = cudaMallocAsync(out, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
     return FP_OK;
@@ -149,7 +164,6 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.heads = f->d_image + h.off_heads;
     p.bins = reinterpret_cast<const FpBin *>(f->d_image + h.off_bins);
     p.passes = reinterpret_cast<const FpPass *>(f->d_image + h.off_passes);
-    p.tree_base = reinterpret_cast<const uint32_t *>(f->d_image + h.off_tree_base);
     p.pheads = reinterpret_cast<const int32_t *>(f->d_image + h.off_pheads);
     p.deep_leaf = reinterpret_cast<const int32_t *>(f->d_image + h.off_deep_leaf);
     p.X = X;
@@ -160,8 +174,12 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.R = f->R;
     p.n_tiles = (n + f->R - 1) / f->R;
     p.head_smem = f->head_smem;
+    p.levels = h.head_select == 1;
+    p.depth = h.depth;
     p.refill = f->refill;
     p.status = f->d_status;
+    p.spin_limit = f->spin_limit;
+    p.stall = f->stall;
     return p;
 }
 
@@ -200,6 +218,7 @@ extern "C" int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_for
     int rc = FP_OK;
     cudaError_t e = cudaGetDevice(&f->device);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGetDevice"); goto fail; }
+    if (injected_alloc_failure("cudaMalloc(image)")) { rc = FP_ENOMEM; goto fail; }
     e = cudaMalloc(&f->d_image, (size_t)h->total_bytes);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(image)"); goto fail; }
     e = cudaMalloc(&f->d_status, 256);
@@ -406,6 +425,27 @@ extern "C" int fp_sync_status(const fp_device_forest *f, void *stream) {
         return word < 0 ? word : FP_EDEVICE;
     }
     return FP_OK;
+}
+
+extern "C" int fp_inject_fault(fp_device_forest *f, int32_t kind, int64_t value) {
+    switch (kind) {
+    case FP_FAULT_ALLOC:
+        if (value < 0) break;
+        g_fail_allocs.store(value);
+        return FP_OK;
+    case FP_FAULT_WAIT_LIMIT:
+        if (!f || value < 1 || value > FP_SPIN_LIMIT) break;
+        f->spin_limit = (int32_t)value;
+        return FP_OK;
+    case FP_FAULT_STALL_BIN_COPY:
+        if (!f || (value != 0 && value != 1)) break;
+        f->stall = (int32_t)value;
+        return FP_OK;
+    default:
+        break;
+    }
+    fp_set_error("fp_inject_fault: bad kind %d, value %lld or forest", kind, (long long)value);
+    return FP_EINVAL;
 }
 
 extern "C" int fp_device_info_get(const fp_device_forest *f, fp_packed_info *info) {

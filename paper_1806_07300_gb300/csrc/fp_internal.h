@@ -13,18 +13,29 @@
 //                                    node[rank*stride + k] = rank-th head node of tree k
 //                                  nexits*stride exit references (4 B):
 //                                    exit[e*stride + k]   = e-th exit of tree k
-//   deep     FpSuper[]           per tree, its super-nodes in Stat order
+//   deep     FpSuper[]           per tree, its super-nodes in Stat order; the
+//                                trees' regions follow one another
 //   --- end of the classification part (class_bytes) ---
 //   parity blocks                per bin, int32 leaf id of each exit (or -1),
 //                                [nexits][stride] like the exits
 //   deep_leaf int32[4] per super-node: leaf id behind each exit, or -1
 //
-// Head of a tree: the K = 2^(d+1) - 1 internal nodes of highest training
-// cardinality (ties: shallower, then earlier), a subtree that contains the
-// root; for a complete tree these are exactly levels 0..d.  They are ranked
-// in depth-first order that visits the more frequently reached child first.
+// Two kinds of head (the header's head_select, the same for every bin):
 //
-// Head node {float thr; uint32 meta}:
+// head_select = 1, levels (the Bin layout of Section III-A): levels 0..d of
+// every tree in implicit breadth-first slots, nranks = 2^(d+1) - 1 and
+// nexits = 2^(d+1) for every bin.  Slot s has children 2s+1 (left) and 2s+2
+// (right); slot nranks + e is exit e.  A leaf above level d+1 fills its slot
+// with a dummy node and every exit below it names the leaf, so whichever way
+// the dummy compares go the walk ends on that leaf; every walk takes exactly
+// d+1 steps.  Head node {float thr; uint32 meta}, meta[31:22] = feature, the
+// rest zero.  d <= FP_MAX_LEVEL_DEPTH.
+//
+// head_select = 0, ranked: the K = 2^(d+1) - 1 internal nodes of highest
+// training cardinality (ties: shallower, then earlier), a subtree that
+// contains the root; for a complete tree these are exactly levels 0..d.
+// They are ranked in depth-first order that visits the more frequently
+// reached child first.  Head node {float thr; uint32 meta}:
 //   [31:22] feature
 //   [21:11] right target, [10:0] left target: a target below the bin's
 //           nranks is the rank of a head node, otherwise it names
@@ -34,7 +45,7 @@
 //
 // A reference (exit entry or super-node exit) is a uint32:
 //   bit 31 = 1: a leaf, bits 30..0 = its class
-//   bit 31 = 0: a tree-local super-node index
+//   bit 31 = 0: a super-node, the index into deep[] (so fewer than 2^31)
 //
 // Super-node (32 bytes, one L2 sector, 32-byte aligned): a node v below the
 // head together with its two children, i.e. two levels of the tree resolved
@@ -49,12 +60,13 @@
 #include <stdint.h>
 
 #define FP_IMAGE_MAGIC 0x4B435046u /* "FPCK" */
-#define FP_IMAGE_VERSION 4u
+#define FP_IMAGE_VERSION 5u
 
 #define FP_MAX_FEATURES 1024
 #define FP_MAX_CLASSES 512
 #define FP_REF_LEAF 0x80000000u
-#define FP_MAX_DEPTH 9
+#define FP_MAX_DEPTH 9         // ranked heads
+#define FP_MAX_LEVEL_DEPTH 11  // level heads
 #define FP_TARGET_BITS 11
 #define FP_TARGET_MASK 2047u
 
@@ -82,7 +94,7 @@ struct FpImageHeader {
     int32_t n_trees, n_features, n_classes;
     int32_t bin_size, depth, n_bins, n_passes;
     int32_t head_nodes;            // K, head nodes per tree at most
-    int32_t head_select;           // 0: highest cardinality, 1: complete levels 0..d
+    int32_t head_select;           // 0: ranked (highest cardinality), 1: levels 0..d in implicit slots
     int32_t obs_tile, warps_per_cta;
     int32_t max_head_bytes;
     int32_t refill_lanes;

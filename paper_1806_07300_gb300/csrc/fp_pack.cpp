@@ -4,11 +4,12 @@
 // each bin's interleaved block in shared memory and reads the rest of a tree
 // in 32-byte sectors:
 //   Bin  (Section III-A, Fig. 2, Fig. 3): trees [bB, (b+1)B) form bin b; the
-//        heads of the bin's trees -- the 2^(d+1)-1 most frequently visited
-//        nodes of each tree, which for a complete tree are levels 0..d -- are
-//        interleaved rank by rank (node[rank*stride + k]), so the roots of
-//        all trees of a bin are contiguous (Fig. 2: depth 0 = roots only) and
-//        the block is staged into shared memory in one piece;
+//        heads of the bin's trees are interleaved node by node
+//        (node[slot*stride + k]), so the roots of all trees of a bin are
+//        contiguous (Fig. 2: depth 0 = roots only) and the block is staged
+//        into shared memory in one piece.  A head is either levels 0..d in
+//        implicit breadth-first slots (the paper's interleaved levels) or the
+//        2^(d+1)-1 most frequently visited nodes of the tree, ranked;
 //   DF-  (Section III-A): leaves are not stored as nodes; a reference to a
 //        leaf carries its class (the paper's shared per-class nodes, folded
 //        into the reference so no load is spent on them);
@@ -114,6 +115,7 @@ int validate_tree(const TreeRef &t, int32_t F, int32_t C, int32_t ti, std::vecto
 }
 
 struct TreeLayout {
+    std::vector<int32_t> slot;       // level heads: node id per implicit slot (a leaf = dummy slot)
     std::vector<int32_t> head;       // node id per head rank
     std::vector<uint32_t> head_meta; // unused (kept zero); targets are encoded per bin
     std::vector<int32_t> rank;       // node id -> head rank (-1 outside the head)
@@ -134,10 +136,11 @@ int64_t card_of(const TreeRef &t, int32_t v) { return t.Card ? t.Card[v] : 0; }
 
 int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti);
 
-// Head: the K internal nodes of highest training cardinality (ties:
+// Head, when select_levels is set: levels 0..d in K = 2^(d+1)-1 implicit
+// breadth-first slots (the interleaved levels of the Bin layout).
+// Otherwise: the K internal nodes of highest training cardinality (ties:
 // shallower, then lower node id) -- the most popular paths of Section III-A,
-// kept in fast memory -- or, when select_levels is set, the internal nodes of
-// levels 0..d.  Both sets contain every ancestor of their members.  They are
+// kept in fast memory -- which contain every ancestor of their members,
 // ranked depth-first, more frequently reached child first (Stat), so the
 // first child visited inside the head sits at the next rank.  Below the head
 // the tree is cut into super-nodes (a node and its two children: one 32-byte
@@ -145,6 +148,25 @@ int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti);
 // cardinality right after its parent (Stat at super-node granularity).
 int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, TreeLayout &out, int32_t ti) {
     const int32_t m = (int32_t)t.m;
+    if (select_levels) {
+        // implicit breadth-first slots of levels 0..d; a leaf above level d+1
+        // is carried down both sides, so its slot is a dummy and every exit
+        // below it names the leaf
+        const int32_t S = K;
+        out.slot.assign((size_t)S, 0);
+        out.exits.assign((size_t)S + 1, 0);
+        for (int32_t s = 0; s < S; ++s) {
+            const int32_t v = out.slot[s];
+            const int32_t kid[2] = {t.leaf(v) ? v : t.L[v], t.leaf(v) ? v : t.R[v]};
+            for (int q = 0; q < 2; ++q) {
+                const int32_t c = 2 * s + 1 + q;
+                if (c < S) out.slot[c] = kid[q];
+                else out.exits[c - S] = kid[q];
+            }
+        }
+        out.head.clear();
+        return finish_super(t, out, ti);
+    }
     std::vector<int32_t> depth((size_t)m, 0);
     std::vector<int32_t> order;  // breadth-first
     order.reserve((size_t)m);
@@ -253,11 +275,14 @@ int finish_super(const TreeRef &t, TreeLayout &out, int32_t ti) {
     return FP_OK;
 }
 
-uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v) {
-    return t.leaf(v) ? (FP_REF_LEAF | (uint32_t)t.Cl[v]) : (uint32_t)lay.sn_index[v];
+// A leaf's class, or the global index of the super-node rooted at v (base =
+// the tree's first super-node).
+uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base) {
+    return t.leaf(v) ? (FP_REF_LEAF | (uint32_t)t.Cl[v]) : (uint32_t)(base + lay.sn_index[v]);
 }
 
-void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, FpSuper &sn, int32_t leaf_ids[4]) {
+void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base, FpSuper &sn,
+                  int32_t leaf_ids[4]) {
     const int32_t l = t.L[v], r = t.R[v];
     float th0 = t.Th[v], th1 = t.leaf(l) ? 0.0f : t.Th[l], th2 = t.leaf(r) ? 0.0f : t.Th[r];
     memcpy(&sn.w[0], &th0, 4);
@@ -268,7 +293,7 @@ void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, FpSuper &s
     int32_t e[4];
     super_exits(t, v, e);
     for (int q = 0; q < 4; ++q) {
-        sn.w[4 + q] = ref_of(t, lay, e[q]);
+        sn.w[4 + q] = ref_of(t, lay, e[q], base);
         leaf_ids[q] = t.leaf(e[q]) ? e[q] : -1;
     }
 }
@@ -309,7 +334,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         R = (int32_t)std::max<int64_t>(32, std::min<int64_t>(1024, r));
     }
     const int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
-    if (B < 1 || B > 1024 || d < 0 || d > FP_MAX_DEPTH || W < 1 || W > 32 || R < 32 || R > 2048 || R % 32 ||
+    if (B < 1 || B > 1024 || d < 0 || d > (select_levels ? FP_MAX_LEVEL_DEPTH : FP_MAX_DEPTH) || W < 1 || W > 32 ||
+        R < 32 || R > 2048 || R % 32 ||
         refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 1) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
                      "refill %d, head_select %d)", B, d, R, W, refill, p.head_select);
@@ -362,10 +388,11 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             bn.width = std::min(B, T - b * B);
             bn.stride = bn.width | 1;
             for (int32_t k = 0; k < bn.width; ++k) {
-                bn.nranks = std::max<int32_t>(bn.nranks, (int32_t)lays[bn.first_tree + k].head.size());
+                bn.nranks = std::max<int32_t>(bn.nranks, (int32_t)(select_levels ? lays[bn.first_tree + k].slot.size()
+                                                                                  : lays[bn.first_tree + k].head.size()));
                 bn.nexits = std::max<int32_t>(bn.nexits, (int32_t)lays[bn.first_tree + k].exits.size());
             }
-            if (bn.nranks + bn.nexits > (int32_t)FP_TARGET_MASK + 1) {
+            if (!select_levels && bn.nranks + bn.nexits > (int32_t)FP_TARGET_MASK + 1) {
                 fp_set_error("fp_pack_forest: bin %d needs %d head targets (at most %u); lower interleave_depth", b,
                              bn.nranks + bn.nexits, FP_TARGET_MASK + 1);
                 return FP_EUNSUPPORTED;
@@ -386,8 +413,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         std::vector<int64_t> tree_base((size_t)T + 1, 0);
         for (int32_t t = 0; t < T; ++t) tree_base[t + 1] = tree_base[t] + deep_count[t];
         const int64_t n_deep = tree_base[T];
-        if (n_deep > (int64_t)UINT32_MAX) {
-            fp_set_error("fp_pack_forest: %lld super-nodes exceed the 32-bit tree base", (long long)n_deep);
+        if (n_deep >= (int64_t)FP_REF_LEAF) {
+            fp_set_error("fp_pack_forest: %lld super-nodes exceed the 31-bit references", (long long)n_deep);
             return FP_EUNSUPPORTED;
         }
         // passes: consecutive bins whose records fit the budget
@@ -451,6 +478,22 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 TreeRef tr{desc->left + nb, desc->right + nb, desc->feature + nb, desc->leaf_class + nb,
                            desc->threshold + nb, nullptr, desc->tree_node_begin[t + 1] - nb};
                 const TreeLayout &lay = lays[t];
+                if (select_levels) {
+                    for (size_t s = 0; s < lay.slot.size(); ++s) {
+                        const int32_t v = lay.slot[s];
+                        const float thr = tr.leaf(v) ? 0.0f : tr.Th[v];
+                        const uint32_t meta = tr.leaf(v) ? 0u : (uint32_t)tr.Fe[v] << 22;
+                        uint8_t *rec = blk + ((int64_t)s * bn.stride + k) * 8;
+                        memcpy(rec, &thr, 4);
+                        memcpy(rec + 4, &meta, 4);
+                    }
+                    for (size_t e = 0; e < lay.exits.size(); ++e) {
+                        const int32_t v = lay.exits[e];
+                        exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v, tree_base[t]);
+                        pexits[(int64_t)e * bn.stride + k] = tr.leaf(v) ? v : -1;
+                    }
+                    continue;
+                }
                 // exit index of each (node, side), in the order layout_tree made them
                 size_t next_exit = 0;
                 for (size_t i = 0; i < lay.head.size(); ++i) {
@@ -477,7 +520,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 }
                 for (size_t e = 0; e < lay.exits.size(); ++e) {
                     const int32_t v = lay.exits[e];
-                    exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v);
+                    exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v, tree_base[t]);
                     pexits[(int64_t)e * bn.stride + k] = tr.leaf(v) ? v : -1;
                 }
             }
@@ -494,7 +537,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             const TreeLayout &lay = lays[t];
             for (size_t i = 0; i < lay.sn_root.size(); ++i) {
                 const int64_t g = tree_base[t] + (int64_t)i;
-                encode_super(tr, lay, lay.sn_root[i], deep[g], dleaf + 4 * g);
+                encode_super(tr, lay, lay.sn_root[i], tree_base[t], deep[g], dleaf + 4 * g);
             }
         }
         *out = pf;

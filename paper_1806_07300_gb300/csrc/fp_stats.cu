@@ -1,6 +1,6 @@
 // fp_stats.cu -- statistics inferred from observations (Section III-A: the
-// leaf cardinalities that order a tree's nodes "can also be inferred after
-// training using a suitably large set of observations").
+// leaf cardinalities that order a tree's nodes need not come from training;
+// they may be estimated afterwards by classifying many observations).
 //
 // fp_count_leaves turns the leaf ids that fp_predict_leaves wrote for a
 // sample of observations into per-node visit counts of the leaves; summing a

@@ -16,9 +16,11 @@
 //   3. walks (observation, tree) tasks in two kinds of warp steps:
 //        burst -- the warp claims 32 consecutive tasks (32 rows of one tree)
 //                 and all lanes walk their paths through the tree's head in
-//                 shared memory together, with a branch-free step; paths that
-//                 leave the head are pushed, compacted with __ballot_sync /
-//                 __popc, into the warp's ring of pending tasks;
+//                 shared memory together, with a branch-free step (level
+//                 heads: exactly d+1 steps over implicit slots; ranked heads:
+//                 until the last lane leaves the head); paths that leave the
+//                 head are pushed, compacted with __ballot_sync / __popc,
+//                 into the warp's ring of pending tasks;
 //        deep  -- every lane holding a task resolves two more levels with one
 //                 32-byte super-node load (one L2 sector); a lane that reaches
 //                 a leaf votes and takes the next pending task from the ring.
@@ -35,11 +37,14 @@
 // Parity mode writes the leaf id reached in every (observation, tree)
 // instead of voting.
 //
-// Waits: cp.async.wait_group and __syncthreads are hardware waits; the
-// mbarrier waits poll at most FP_SPIN_LIMIT times, then record FP_ETIMEOUT in
-// the status word and make every warp skip the rest of its work (and wait,
-// again bounded, for the CTA's own bulk copies before exiting).  Every walk is
-// bounded too.
+// Waits: cp.async.wait_group and __syncthreads are hardware waits; a wait for
+// a bin block polls its mbarrier at most spin_limit times (FP_SPIN_LIMIT
+// unless a test lowers it), then records FP_ETIMEOUT in the status word and
+// makes every warp skip the rest of its work; before exiting, the CTA waits
+// (bounded by FP_SPIN_LIMIT polls) for its own bulk copies to land.  A test
+// can set `stall` so that bin waits ignore completed copies and run out; the
+// copies themselves still complete, so the exit path stays clean.  Every walk
+// is bounded too.
 #pragma once
 #include <stdint.h>
 
@@ -50,7 +55,6 @@ struct TravParams {
     const uint8_t *heads;     // interleaved blocks
     const FpBin *bins;
     const FpPass *passes;
-    const uint32_t *tree_base;
     const int32_t *pheads;    // parity: leaf id per block exit
     const int32_t *deep_leaf; // parity: 4 leaf ids per super-node
     const float *X;
@@ -60,6 +64,8 @@ struct TravParams {
     int32_t F, C, T, R;
     int32_t n_passes;
     int32_t head_smem;        // bytes reserved for one bin block
+    int32_t levels;           // 1: level heads (implicit slots, depth+1 steps); 0: ranked heads
+    int32_t depth;            // d of the interleaved head
     int32_t refill;           // bursts start when the ring holds at most this many tasks
     uint32_t *out_votes;      // single pass: final votes (may be NULL)
     int32_t *out_class;       // may be NULL
@@ -67,6 +73,8 @@ struct TravParams {
     uint32_t *acc;            // several passes: vote accumulator
     uint32_t *tile_done;      // several passes: per-tile pass counter
     int32_t *status;          // device status word
+    int32_t spin_limit;       // polls of a bin block's barrier before the wait gives up
+    int32_t stall;            // fault injection: bin waits ignore completed copies (0 normally)
 };
 
 #define FP_ERR_FLAG_DEVICE (-6)
@@ -90,10 +98,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // One super-node: a single 256-bit load (32-byte aligned, one L2 sector).
-// The memory clobber keeps the load where it is written, ahead of the work
-// meant to overlap its latency.
+// The lines are not allocated in L1: few super-nodes are read twice by one
+// SM before eviction, and with most of the unified L1/shared array given to
+// shared memory, allocating a line per lane for thousands of loads in
+// flight throttles the load path (measured: twice the run time once shared
+// memory takes more than about 196 KB).  The memory clobber keeps the load
+// where it is written, ahead of the work meant to overlap its latency.
 __device__ __forceinline__ void ld_super(const FpSuper *p, uint32_t w[8]) {
-    asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                  : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
                  : "l"(p)
                  : "memory");
@@ -138,9 +150,7 @@ struct LaneTask {
     bool active;
     int r;            // row within the tile
     int t;            // tree
-    uint32_t ref;     // current super-node (tree-local)
-    uint32_t steps;
-    const FpSuper *tb;
+    uint32_t ref;     // current super-node (index into deep)
 };
 
 // A finished task: vote, or record the leaf id in parity mode.
@@ -168,8 +178,6 @@ __device__ __forceinline__ void pop_tasks(const TravParams &p, const uint2 *ring
         L.ref = ent.x;
         L.r = (int)(ent.y & 2047u);
         L.t = (int)(ent.y >> 11);
-        L.tb = p.deep + p.tree_base[L.t];
-        L.steps = 0;
         L.active = true;
     }
     head += npop;
@@ -178,7 +186,9 @@ __device__ __forceinline__ void pop_tasks(const TravParams &p, const uint2 *ring
 // One deep step, two levels of the tree per 32-byte load, in two halves: the
 // load is issued first and consumed after the warp has done other work (a
 // head burst), so the L2 latency overlaps that work.
-__device__ __forceinline__ void deep_issue(const LaneTask &L, uint32_t w[8]) { ld_super(L.tb + L.ref, w); }
+__device__ __forceinline__ void deep_issue(const TravParams &p, const LaneTask &L, uint32_t w[8]) {
+    ld_super(p.deep + L.ref, w);
+}
 
 template <bool LEAVES>
 __device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
@@ -194,7 +204,7 @@ __device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs
     if (nref & FP_REF_LEAF) {
         L.active = false;
         int32_t leaf_id = -1;
-        if (LEAVES) leaf_id = p.deep_leaf[4 * ((int64_t)(L.tb - p.deep) + L.ref) + 2 * d0 + d1];
+        if (LEAVES) leaf_id = p.deep_leaf[4 * (int64_t)L.ref + 2 * d0 + d1];
         finish<LEAVES>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
     } else if (nref > L.ref) {  // super-nodes only point forward, so every walk ends
         L.ref = nref;
@@ -264,6 +274,14 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         stage_block_bulk(p, b, hbuf0 + buf * p.head_smem, &sh.full[buf]);
     };
 
+    // A CTA that gave up a wait skips its remaining items; each one records
+    // the timeout in its own forest's status, since its outputs stay unwritten
+    // (sh.abort is uniform here: it changes only inside the bin loop, and the
+    // previous item ended with a CTA barrier).
+    if (*(volatile int *)&sh.abort) {
+        if (tid == 0) report(p.status, FP_ERR_FLAG_TIMEOUT);
+        return;
+    }
     const int pass = (int)(item / p.n_tiles);
     const int64_t tile = item - (int64_t)pass * p.n_tiles;
     const int64_t row0 = tile * R;
@@ -294,8 +312,6 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     L.r = 0;
     L.t = 0;
     L.ref = 0;
-    L.steps = 0;
-    L.tb = p.deep;
     int head = 0, tail = 0;  // warp-uniform ring cursors
 
     for (int bi = 0; bi < nbins; ++bi) {
@@ -304,9 +320,9 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         {  // wait until the bin's block has landed
             const uint32_t parity = (seq / FP_NBUF) & 1u;
             bool ok = false;
-            for (int spin = 0; spin < FP_SPIN_LIMIT; ++spin) {
+            for (int spin = 0; spin < p.spin_limit; ++spin) {
                 if (*(volatile int *)&sh.abort) break;
-                if (mbar_try_wait(&sh.full[buf], parity)) {
+                if (mbar_try_wait(&sh.full[buf], parity) && !p.stall) {
                     ok = true;
                     break;
                 }
@@ -329,7 +345,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 
         for (;;) {
             uint32_t w[8];
-            if (L.active) deep_issue(L, w);  // in flight during the burst below
+            if (L.active) deep_issue(p, L, w);  // in flight during the burst below
             if (tail - head <= p.refill) {
                 // burst: 32 consecutive tasks through the head, all lanes together
                 int base = 0;
@@ -345,10 +361,18 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     k2 += (k2 + 1) * rows <= task;
                 }
                 const int r2 = my ? task - k2 * rows : 0;
-                uint32_t hr = 0;  // head rank, then nranks + exit index
-                bool busy = my;
+                uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
                 const float *xr = xs + r2;     // this lane's row
+                if (p.levels) {
+                    // implicit slots: every walk takes depth+1 steps, children 2s+1, 2s+2
+                    for (int l = 0; l <= p.depth; ++l) {
+                        const uint2 nd = hn[hr * stride];
+                        const float xv = xr[(nd.y >> 22) * R];
+                        hr = 2 * hr + (xv <= __uint_as_float(nd.x) ? 1u : 2u);
+                    }
+                }
+                bool busy = my && !p.levels;
                 while (__any_sync(0xffffffffu, busy)) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {  // two steps per vote
@@ -405,7 +429,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         if (!__any_sync(0xffffffffu, L.active)) break;
         if (L.active) {
             uint32_t w[8];
-            deep_issue(L, w);
+            deep_issue(p, L, w);
             deep_finish<LEAVES>(p, xs, svotes, row0, L, w);
         }
     }

@@ -63,7 +63,13 @@ class Image:
                 t = int(bn["first_tree"]) + k
                 nr = int(bn["nranks"])
                 hr = np.zeros(n, np.int64)
-                busy = np.ones(n, bool)
+                if g["head_select"] == 1:  # implicit slots: children 2s+1 and 2s+2, d+1 steps
+                    assert nr == 2 ** (g["depth"] + 1) - 1
+                    for _ in range(g["depth"] + 1):
+                        m = meta[hr, k].astype(np.int64)
+                        right = ~(X[rows, m >> 22] <= thr[hr, k])
+                        hr = 2 * hr + 1 + right
+                busy = np.full(n, g["head_select"] != 1)
                 while np.any(busy):
                     a = rows[busy]
                     m = meta[hr[a], k].astype(np.int64)
@@ -76,11 +82,10 @@ class Image:
                 cls[lf, t] = (ref[lf] & 0x7FFFFFFF).astype(np.int32)
                 leaf[lf, t] = par[e[lf], k]
                 state = np.where(lf, 2, 1).astype(np.int8)
-                idx = np.where(lf, -1, ref.astype(np.int64))
-                base = int(self.tree_base[t])
+                idx = np.where(lf, -1, ref.astype(np.int64))  # super-node references are global
                 while np.any(state == 1):
                     a = rows[state == 1]
-                    g_idx = base + idx[a]
+                    g_idx = idx[a]
                     w = self.sw[g_idx]
                     th = self.sthr[g_idx]
                     f0 = (w[:, 3] & 1023).astype(np.int64)

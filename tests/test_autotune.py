@@ -18,10 +18,11 @@ def test_block_bytes_formula():
 def test_candidate_layouts_pack(tiny_forest):
     cands = at.candidate_layouts(tiny_forest.n_trees)
     assert 2 <= len(cands) <= 10
-    for B, d in cands:
-        assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= 9
+    assert {sel for _, _, sel in cands} == {0, 1}
+    for B, d, sel in cands:
+        assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (11 if sel else 9)
         assert at.block_bytes(B, d) <= 48 * 1024 or d == 0
-        fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d)
+        fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
 
 
 def test_candidate_launches():
@@ -47,11 +48,11 @@ def test_autotune_tiny_on_gpu(tiny_forest, tiny_rows, tmp_path, monkeypatch):
     monkeypatch.setenv("FP_CACHE_DIR", str(tmp_path))
     X, _ = tiny_rows
     Xd = torch.from_numpy(X).cuda()
-    best = at.autotune(tiny_forest, Xd, layouts=[(1, 3), (16, 4), (4, 6)],
+    best = at.autotune(tiny_forest, Xd, layouts=[(1, 3), (16, 4, 1), (4, 6, 0), (2, 7, 1)],
                        launches=[(256, 16, 16), (128, 32, 32)])
-    assert best["ms"] > 0 and len(best["table"]) == 6
+    assert best["ms"] > 0 and len(best["table"]) == 8
     again = at.autotune(tiny_forest, Xd, layouts=[(1, 0)])  # served from the cache
-    assert again["bin_size"] == best["bin_size"] and again["interleave_depth"] == best["interleave_depth"]
+    assert all(again[k] == best[k] for k in at.LAYOUT_KEYS)
     df, _ = at.upload_tuned(tiny_forest, Xd)
     v, c = df.predict(Xd)
     torch.cuda.synchronize()

@@ -1,7 +1,8 @@
-"""Full-size parity at the launch configuration bench.py times.
+"""Full-size parity at the launch configurations bench.py times.
 
-The HBM-resident workload (256 trees, 4,000,000 rows) and the image-shaped
-workload (128 trees, 1,000,000 rows) run exactly as the benchmark runs them.
+The HBM-resident workload (256 trees, 4,000,000 rows) runs in every layout and
+launch the benchmark's autotuner may pick, and the image-shaped workload (128
+trees, 1,000,000 rows) in the library defaults and the tuner's candidates.
 Every row is checked against properties that hold at any size (votes sum to
 the tree count; the class is the first maximal vote); a seeded sample of rows
 is checked element by element against the oracle, votes, classes and per-tree
@@ -12,6 +13,8 @@ import pytest
 import datagen
 import oracle
 import paper_1806_07300_gb300 as fp
+from bench import HBM_LAUNCHES, HBM_LAYOUTS
+from paper_1806_07300_gb300 import autotune as at
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,11 +29,25 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _run(name, n):
-    forest = datagen.forest(name)
-    X, _ = datagen.test_rows(name, n)
-    df = fp.fp_upload(fp.fp_pack_forest(forest))  # the benchmark's default parameters
-    Xd = torch.from_numpy(X).cuda()
+_DATA = {}
+
+
+def _data(name, n):
+    if name not in _DATA:
+        _DATA.clear()
+        X, _ = datagen.test_rows(name, n)
+        _DATA[name] = (datagen.forest(name), X, torch.from_numpy(X).cuda())
+    return _DATA[name]
+
+
+def _run(name, n, layout=None, launch=None):
+    forest, X, Xd = _data(name, n)
+    params = {}
+    if layout is not None:
+        params = dict(zip(at.LAYOUT_KEYS, layout))
+    df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
+    if launch is not None:
+        df.configure(**dict(zip(at.LAUNCH_KEYS, launch)))
     votes, cls = df.predict(Xd)
     torch.cuda.synchronize()
     assert df.sync_status() == fp.FP_OK
@@ -52,9 +69,12 @@ def _run(name, n):
     df.release()
 
 
-def test_hbm_workload_full_size():
-    _run("hbm", datagen.RECIPES["hbm"]["n_test"])
+@pytest.mark.parametrize("layout", HBM_LAYOUTS)
+def test_hbm_workload_full_size(layout):
+    for launch in HBM_LAUNCHES:
+        _run("hbm", datagen.RECIPES["hbm"]["n_test"], layout, launch)
 
 
-def test_image_workload_full_size():
-    _run("image", datagen.RECIPES["image"]["n_test"])
+@pytest.mark.parametrize("layout", [None, (16, 5, 1), (2, 8, 0)])
+def test_image_workload_full_size(layout):
+    _run("image", datagen.RECIPES["image"]["n_test"], layout)

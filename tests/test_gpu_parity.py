@@ -50,18 +50,20 @@ def _check_all(forest, X, ref=None, **params):
 
 
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
-@pytest.mark.parametrize("B,d", [(1, 0), (2, 1), (3, 3)])
-def test_hand_fixtures_on_gpu(name, B, d):
-    """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs."""
+@pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 1, 0), (3, 3, 0), (1, 0, 1), (2, 3, 1)])
+def test_hand_fixtures_on_gpu(name, B, d, sel):
+    """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs; ranked
+    heads (sel 0) and level heads (sel 1)."""
     forest, X, exp = load(name)
     ref = dict(leaf=exp["leaf"], votes=exp["votes"], cls=exp["cls"])
-    _check_all(forest, X, ref, bin_size=B, interleave_depth=d)
+    _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel)
 
 
-@pytest.mark.parametrize("B,d", [(16, 4), (1, 0), (5, 2), (7, 6), (4, 9)])
-def test_tiny_workload(tiny_forest, tiny_rows, B, d):
+@pytest.mark.parametrize("B,d,sel", [(16, 4, 0), (1, 0, 0), (5, 2, 0), (7, 6, 0), (4, 9, 0), (16, 4, 1), (1, 0, 1),
+                                     (3, 8, 1), (1, 11, 1)])
+def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel):
     X, _ = tiny_rows
-    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d)
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel)
 
 
 @pytest.mark.parametrize("tile,warps", [(32, 1), (64, 3), (256, 8), (1024, 32)])
@@ -71,12 +73,13 @@ def test_tiny_tiles_and_ragged_tail(tiny_forest, tiny_rows, tile, warps):
 
 
 @pytest.mark.parametrize("pass_bytes", [1, 2048, 8192])
-def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes):
+@pytest.mark.parametrize("sel", [0, 1])
+def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes, sel):
     """Several passes: global accumulation and last-pass argmax."""
     X, _ = tiny_rows
-    pk = fp.fp_pack_forest(tiny_forest, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes)
+    pk = fp.fp_pack_forest(tiny_forest, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes, head_select=sel)
     assert pk.info()["passes"] > 1
-    _check_all(tiny_forest, X, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes, obs_tile=128)
+    _check_all(tiny_forest, X, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes, obs_tile=128, head_select=sel)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33])
@@ -151,5 +154,5 @@ def test_image_workload_params_grid():
     forest = datagen.forest("image")
     X, _ = datagen.test_rows("image", 3000)
     ref = oracle.predict(forest, X, threads=oracle.default_threads())
-    for B, d in [(128, 1), (16, 3), (8, 5), (1, 9)]:
-        _check_all(forest, X, ref, bin_size=B, interleave_depth=d)
+    for B, d, sel in [(128, 1, 0), (16, 3, 0), (8, 5, 0), (1, 9, 0), (16, 5, 1), (1, 10, 1)]:
+        _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel)

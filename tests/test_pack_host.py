@@ -39,19 +39,21 @@ def test_binding_has_no_cpu_path():
 
 
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
-@pytest.mark.parametrize("B,d", [(1, 0), (2, 0), (2, 1), (3, 2), (1, 5)])
-def test_packed_records_decode_to_fixture_leaves(name, B, d):
+@pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 0, 0), (2, 1, 0), (3, 2, 0), (1, 5, 0), (1, 0, 1), (2, 1, 1),
+                                     (3, 4, 1)])
+def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
     forest, X, exp = load(name)
-    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d)
+    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel)
     leaf, cls = Image(pk.image()).walk(X)
     np.testing.assert_array_equal(leaf, exp["leaf"])
 
 
-@pytest.mark.parametrize("B,d", [(16, 4), (5, 0), (1, 2), (7, 7)])
-def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d):
+@pytest.mark.parametrize("B,d,sel", [(16, 4, 0), (5, 0, 0), (1, 2, 0), (7, 7, 0), (16, 4, 1), (3, 0, 1), (1, 9, 1),
+                                     (1, 11, 1)])
+def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel):
     X, _ = tiny_rows
     ref = oracle.predict(tiny_forest, X[:3000])
-    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d)
+    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
     leaf, cls = Image(pk.image()).walk(X[:3000])
     np.testing.assert_array_equal(leaf, ref["leaf"])
     np.testing.assert_array_equal(cls, tiny_forest.leaf_class[tiny_forest.node_begin[:-1][None, :] + ref["leaf"]])
@@ -86,9 +88,9 @@ def _head_nodes(forest, t, im):
 
 
 def _super_roots(forest, t, im, exit_node):
+    """Global super-node index -> the tree-local node it is rooted at."""
     b, k = t // im.h["bin_size"], t % im.h["bin_size"]
     _, _, exits, _ = im.head(b)
-    base = int(im.tree_base[t])
     tr = forest.tree(t)
     roots = {}
     stack = [(int(exits[e, k]), v) for e, v in exit_node.items() if not int(exits[e, k]) & LEAF]
@@ -99,7 +101,7 @@ def _super_roots(forest, t, im, exit_node):
         ex = [l, l] if tr["left"][l] < 0 else [int(tr["left"][l]), int(tr["right"][l])]
         ex += [r, r] if tr["left"][r] < 0 else [int(tr["left"][r]), int(tr["right"][r])]
         for q in range(4):
-            ref = int(im.sw[base + i, 4 + q])
+            ref = int(im.sw[i, 4 + q])
             if not ref & LEAF:
                 stack.append((ref, ex[q]))
     return roots
@@ -133,20 +135,38 @@ def test_head_is_top_cardinality_and_stat_ranked(tiny_forest, d):
                     assert tr["cardinality"][head[i + 1]] >= tr["cardinality"][other]
 
 
-def test_head_select_levels(tiny_forest):
+@pytest.mark.parametrize("d", [0, 3, 6])
+def test_head_select_levels(tiny_forest, d):
+    """Level heads (the Bin layout's interleaved levels 0..d): slot s of tree k
+    holds the node at breadth-first position s (children 2s+1, 2s+2); below a
+    leaf the slots are dummies and every exit names that leaf; exit e is the
+    node at level d+1, position e."""
     f = tiny_forest
-    d = 3
     im = Image(fp.fp_pack_forest(f, bin_size=5, interleave_depth=d, head_select=1).image())
+    S = 2 ** (d + 1) - 1
     for t in range(f.n_trees):
         tr = f.tree(t)
-        head, _ = _head_nodes(f, t, im)
-        depth = {0: 0}
-        for v in range(len(tr["left"])):
-            if tr["left"][v] >= 0:
-                depth[int(tr["left"][v])] = depth[v] + 1
-                depth[int(tr["right"][v])] = depth[v] + 1
-        want = [v for v in range(len(tr["left"])) if tr["left"][v] >= 0 and depth[v] <= d]
-        assert sorted(head) == sorted(want)
+        thr, meta, exits, par = im.head(t // 5)
+        k = t % 5
+        assert thr.shape[0] == S and exits.shape[0] == S + 1
+        slot = {0: 0}  # slot -> node (a leaf marks a dummy slot)
+        for s in range(S):
+            v = slot[s]
+            leaf = tr["left"][v] < 0
+            if not leaf:
+                assert meta[s, k] >> 22 == tr["feature"][v] and thr[s, k] == tr["threshold"][v]
+                assert meta[s, k] & ((1 << 22) - 1) == 0
+            kids = (v, v) if leaf else (int(tr["left"][v]), int(tr["right"][v]))
+            for q, c in enumerate(kids):
+                slot[2 * s + 1 + q] = c
+        for e in range(S + 1):
+            v = slot[S + e]
+            ref = int(exits[e, k])
+            if tr["left"][v] < 0:
+                assert ref == LEAF | int(tr["leaf_class"][v]) and par[e, k] == v
+            else:
+                assert not ref & LEAF and par[e, k] == -1
+                assert im.sthr[ref, 0] == tr["threshold"][v], "the exit roots the super-node of its node"
 
 
 def test_stat_order_in_super_nodes(tiny_forest):
@@ -162,11 +182,11 @@ def test_stat_order_in_super_nodes(tiny_forest):
         head, exit_node = _head_nodes(f, t, im)
         roots = _super_roots(f, t, im, exit_node)
         base = int(im.tree_base[t])
-        n_t = (int(im.tree_base[t + 1]) if t + 1 < f.n_trees else im.sw.shape[0]) - base
-        assert sorted(roots) == list(range(n_t))
+        end = int(im.tree_base[t + 1]) if t + 1 < f.n_trees else im.sw.shape[0]
+        assert sorted(roots) == list(range(base, end)), "a tree's super-nodes are one contiguous region"
         for i, v in roots.items():
-            kids = sorted({int(im.sw[base + i, 4 + q]) for q in range(4)} - {c for c in
-                          (int(im.sw[base + i, 4 + q]) for q in range(4)) if c & LEAF})
+            kids = sorted({int(im.sw[i, 4 + q]) for q in range(4)} - {c for c in
+                          (int(im.sw[i, 4 + q]) for q in range(4)) if c & LEAF})
             if kids:
                 card = {c: int(tr["cardinality"][roots[c]]) for c in kids}
                 assert i + 1 in kids and card[i + 1] == max(card.values()), "hottest child super-node follows"
@@ -246,8 +266,8 @@ def test_unsupported_sizes_rejected():
     assert ei.value.code == fp.FP_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(obs_tile=33),
-                                dict(warps_per_cta=40)])
+@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(interleave_depth=12, head_select=1),
+                                dict(obs_tile=33), dict(warps_per_cta=40), dict(head_select=2)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(tiny_forest, **kw)
