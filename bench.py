@@ -61,8 +61,8 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-HBM_LAYOUTS = [(3, 8, 1), (2, 9, 1), (1, 10, 1), (16, 5, 1), (3, 8, 0)]  # (B, d, head_select)
-HBM_LAUNCHES = [(768, 32, 16), (1024, 32, 16)]
+HBM_LAYOUTS = [(4, 9, 1), (3, 9, 1), (2, 9, 1), (3, 8, 1), (1, 10, 1), (16, 5, 1), (3, 8, 0)]  # (B, d, head_select)
+HBM_LAUNCHES = [(768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3), (1024, 32, 16, 3)]  # tile, warps, refill, buffers
 
 
 def parse():
@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--bin-buffers", type=int, default=0)
     ap.add_argument("--pass-bytes", type=int, default=0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
@@ -253,7 +254,8 @@ def tuned_forest(args, forest, X, name):
         params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes,
                       head_select=args.head_select)
         df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
-        df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill)
+        df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill,
+                     bin_buffers=args.bin_buffers)
     else:
         sample = X[: min(X.shape[0], 1 << 20)]
         layouts = HBM_LAYOUTS if name == "hbm" else None
@@ -379,7 +381,7 @@ def run_packed(args, ws, rank, local):
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "obs_tile", "warps_per_cta",
-                                   "refill_lanes")}
+                                   "refill_lanes", "bin_buffers")}
     traffic = profiled_traffic(name, params, n)
     out = base_line(args, ws, value, total_ms,
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,

@@ -79,7 +79,8 @@ typedef struct fp_forest_desc {
  *   bin_size          B, trees per bin (Section III-A "stripe width"), 1..1024
  *   interleave_depth  d: each tree contributes 2^(d+1)-1 nodes (levels 0..d of
  *                     a complete tree) to its bin's interleaved block
- *                     (Section III-A), 0..9
+ *                     (Section III-A), 0..9 for ranked heads, 0..11 for
+ *                     level heads
  *   obs_tile          observations per work item of the traversal kernel,
  *                     a multiple of 32, up to 2048
  *   warps_per_cta     warps per CTA of the traversal kernel, 1..32
@@ -90,8 +91,14 @@ typedef struct fp_forest_desc {
  *   refill_lanes      a warp hands new (observation, tree) tasks to its idle
  *                     lanes once this many lanes are idle, 1..32
  *   head_select       which 2^(d+1)-1 nodes of a tree form its interleaved head:
- *                     0 = those of highest training cardinality (the popular
- *                     paths of Section III-A), 1 = levels 0..d exactly */
+ *                     0 = ranked: those of highest training cardinality (the
+ *                     popular paths of Section III-A), walked by explicit
+ *                     targets; 1 = levels 0..d in implicit breadth-first
+ *                     slots (the Bin layout's interleaved levels; every walk
+ *                     takes d+1 steps)
+ *   bin_buffers       shared-memory buffers that bin blocks stream through,
+ *                     2 or 3 (0 = 3): two leave room for larger heads or
+ *                     tiles, three hide copy latency better */
 typedef struct fp_pack_params {
     int32_t bin_size;
     int32_t interleave_depth;
@@ -100,6 +107,8 @@ typedef struct fp_pack_params {
     int64_t pass_bytes;
     int32_t refill_lanes;
     int32_t head_select;
+    int32_t bin_buffers;
+    int32_t reserved;         /* must be 0 */
 } fp_pack_params;
 
 typedef struct fp_packed_forest fp_packed_forest; /* host image, opaque */
@@ -121,7 +130,7 @@ typedef struct fp_packed_info {
     int32_t refill_lanes;
     int32_t head_nodes;       /* 2^(d+1)-1: head nodes per tree at most */
     int32_t head_select;
-    int32_t reserved;
+    int32_t bin_buffers;
 } fp_packed_info;
 
 /* Build the packed host image of a forest (Section III-A: DF-, Stat, Bin).
@@ -142,15 +151,16 @@ int fp_packed_info_get(const fp_packed_forest *pf, fp_packed_info *info);
 const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes);
 
 /* Copy a packed image to the current device on `stream` and return a
- * resident forest (library-owned until fp_release).  The host image may be
- * released once the call returns (the copy is staged through library-owned
- * pinned memory).  Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA. */
+ * resident forest (library-owned until fp_release).  The call waits for the
+ * copy to finish on `stream`, so the host image may be released once it
+ * returns.  Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA, FP_EUNSUPPORTED (the
+ * launch does not fit shared memory). */
 int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_forest **out);
 
 /* Change the launch parameters of a resident forest: obs_tile,
- * warps_per_cta and refill_lanes of *params (0 keeps the current value); the
- * layout fields (bin_size, interleave_depth, pass_bytes) must be 0 or equal
- * to the forest's.  The observation tile is lowered, if needed, to fit shared
+ * warps_per_cta, refill_lanes and bin_buffers of *params (0 keeps the current
+ * value); the layout fields (bin_size, interleave_depth, pass_bytes) must be 0
+ * or equal to the forest's.  The observation tile is lowered, if needed, to fit shared
  * memory.  Host only; do not call while a launch on this forest is being
  * enqueued from another thread.  Errors: FP_EINVAL, FP_EUNSUPPORTED, FP_ECUDA. */
 int fp_configure(fp_device_forest *forest, const fp_pack_params *params);

@@ -21,8 +21,8 @@ from . import FPError, fp_pack_forest, fp_predict, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
 LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select")
-_SEARCH_VERSION = "levels-v5"  # cached results of an older search space are not reused
-LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes")
+_SEARCH_VERSION = "levels-v5-nbuf"  # cached results of an older search space are not reused
+LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")
 
 
 def block_bytes(bin_size: int, depth: int) -> int:
@@ -52,10 +52,10 @@ def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int 
     return out
 
 
-def candidate_launches(default_tile: int) -> list[tuple[int, int, int]]:
-    """(obs_tile, warps_per_cta, refill_lanes) triples."""
+def candidate_launches(default_tile: int) -> list[tuple[int, int, int, int]]:
+    """(obs_tile, warps_per_cta, refill_lanes, bin_buffers) tuples."""
     tiles = sorted({default_tile, max(32, default_tile // 2 // 32 * 32)}, reverse=True)
-    return [(t, w, r) for t in tiles for w in (32, 16) for r in (32, 16)]
+    return [(t, w, r, nb) for t in tiles for w in (32, 16) for r in (32, 16) for nb in (3, 2)]
 
 
 def forest_key(forest) -> str:
@@ -123,19 +123,21 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
             table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, error=str(e)))
             continue
         pack_s = time.perf_counter() - t0
-        for tile, warps, refill in (launches or candidate_launches(df.info["obs_tile"])):
+        for launch in (launches or candidate_launches(df.info["obs_tile"])):
+            tile, warps, refill = launch[:3]
+            nbuf = launch[3] if len(launch) > 3 else 3
             try:
-                df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill)
+                df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
             except FPError as e:
                 table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=tile,
-                                  warps_per_cta=warps, refill_lanes=refill, error=str(e)))
+                                  warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf, error=str(e)))
                 continue
             ms = _time_predict(df, X, None, cls, reps)
             if ref is None:
                 ref = cls.clone()
             same = bool(torch.equal(ref, cls))
             row = dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=df.info["obs_tile"],
-                       warps_per_cta=warps,
+                       warps_per_cta=warps, bin_buffers=nbuf,
                        refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)
             table.append(row)
             if verbose:

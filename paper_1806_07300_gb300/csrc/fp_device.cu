@@ -31,6 +31,7 @@ struct fp_device_forest {
     int32_t threads = 0;
     int32_t refill = 8;
     int32_t head_smem = 0;
+    int32_t nbuf = 3;                          // bin-block buffers
     size_t smem_votes = 0, smem_leaves = 0;
     int32_t grid_votes = 0, grid_leaves = 0;  // resident CTAs for a persistent launch
     int32_t spin_limit = FP_SPIN_LIMIT;       // fault injection may lower it
@@ -81,11 +82,11 @@ int scratch_alloc(int device, void **out, size_t bytes, cudaStream_t s) {
     return FP_OK;
 }
 
-// rows tile (feature-major) + FP_NBUF bin blocks + votes + per-warp task rings
-size_t smem_bytes(int R, int F, int head_smem, int C, int warps, bool leaves) {
+// rows tile (feature-major) + nbuf bin blocks + votes + per-warp task rings
+size_t smem_bytes(int R, int F, int head_smem, int nbuf, int C, int warps, bool leaves) {
     const size_t xs = ((size_t)R * F * 4 + 15) & ~(size_t)15;
     const size_t votes = leaves ? 0 : (((size_t)R * C * 4 + 15) & ~(size_t)15);
-    return xs + FP_NBUF * (size_t)head_smem + votes + (size_t)warps * FP_RING * 8;
+    return xs + (size_t)nbuf * (size_t)head_smem + votes + (size_t)warps * FP_RING * 8;
 }
 
 // The kernel variant for a block size: up to 512 threads run the three-CTAs-
@@ -115,9 +116,11 @@ int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
 }
 
 // Fit the observation tile to shared memory and size the persistent grid.
-int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refill) {
-    if (tile < 32 || tile > 2048 || tile % 32 || warps < 1 || warps > 32 || refill < 1 || refill > 32) {
-        fp_set_error("launch parameters out of range (obs_tile %d, warps %d, refill %d)", tile, warps, refill);
+int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refill, int32_t nbuf) {
+    if (tile < 32 || tile > 2048 || tile % 32 || warps < 1 || warps > 32 || refill < 1 || refill > 32 ||
+        (nbuf != 2 && nbuf != 3)) {
+        fp_set_error("launch parameters out of range (obs_tile %d, warps %d, refill %d, bin_buffers %d)", tile, warps,
+                     refill, nbuf);
         return FP_EINVAL;
     }
     int max_optin = 0;
@@ -126,18 +129,19 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     const size_t budget = (size_t)max_optin - 256;  // leaves room for the static shared variables
     const int C = f->hdr.n_classes, F = f->hdr.n_features;
     int R = tile;
-    while (R > 32 && smem_bytes(R, F, f->head_smem, C, warps, false) > budget) R -= 32;
-    if (smem_bytes(R, F, f->head_smem, C, warps, false) > budget) {
+    while (R > 32 && smem_bytes(R, F, f->head_smem, nbuf, C, warps, false) > budget) R -= 32;
+    if (smem_bytes(R, F, f->head_smem, nbuf, C, warps, false) > budget) {
         fp_set_error("a 32-row tile, the bin-block buffers and the task rings need %zu bytes of shared memory (limit %zu)",
-                     smem_bytes(R, F, f->head_smem, C, warps, false), budget);
+                     smem_bytes(R, F, f->head_smem, nbuf, C, warps, false), budget);
         return FP_EUNSUPPORTED;
     }
     fp_device_forest g = *f;
     g.R = R;
     g.threads = 32 * warps;
     g.refill = refill;
-    g.smem_votes = smem_bytes(R, F, f->head_smem, C, warps, false);
-    g.smem_leaves = smem_bytes(R, F, f->head_smem, C, warps, true);
+    g.nbuf = nbuf;
+    g.smem_votes = smem_bytes(R, F, f->head_smem, nbuf, C, warps, false);
+    g.smem_leaves = smem_bytes(R, F, f->head_smem, nbuf, C, warps, true);
     int rc = configure<false>(&g, g.smem_votes, &g.grid_votes);
     if (rc) return rc;
     rc = configure<true>(&g, g.smem_leaves, &g.grid_leaves);
@@ -149,6 +153,7 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     f->R = g.R;
     f->threads = g.threads;
     f->refill = g.refill;
+    f->nbuf = g.nbuf;
     f->smem_votes = g.smem_votes;
     f->smem_leaves = g.smem_leaves;
     f->grid_votes = g.grid_votes;
@@ -174,6 +179,7 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.R = f->R;
     p.n_tiles = (n + f->R - 1) / f->R;
     p.head_smem = f->head_smem;
+    p.nbuf = f->nbuf;
     p.levels = h.head_select == 1;
     p.depth = h.depth;
     p.refill = f->refill;
@@ -230,7 +236,7 @@ extern "C" int fp_upload(const fp_packed_forest *pf, void *stream, fp_device_for
     e = cudaStreamSynchronize(s);  // the caller may free the host image on return
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamSynchronize"); goto fail; }
     f->head_smem = (h->max_head_bytes + 15) & ~15;
-    rc = launch_setup(f, h->obs_tile, h->warps_per_cta, h->refill_lanes);
+    rc = launch_setup(f, h->obs_tile, h->warps_per_cta, h->refill_lanes, h->bin_buffers);
     if (rc) goto fail;
     *out = f;
     return FP_OK;
@@ -257,7 +263,8 @@ extern "C" int fp_configure(fp_device_forest *f, const fp_pack_params *params) {
     if (rc) return rc;
     return launch_setup(f, params->obs_tile ? params->obs_tile : f->R,
                         params->warps_per_cta ? params->warps_per_cta : f->threads / 32,
-                        params->refill_lanes ? params->refill_lanes : f->refill);
+                        params->refill_lanes ? params->refill_lanes : f->refill,
+                        params->bin_buffers ? params->bin_buffers : f->nbuf);
 }
 
 extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, uint32_t *out_votes,
@@ -457,6 +464,7 @@ extern "C" int fp_device_info_get(const fp_device_forest *f, fp_packed_info *inf
     info->obs_tile = f->R;
     info->warps_per_cta = f->threads / 32;
     info->refill_lanes = f->refill;
+    info->bin_buffers = f->nbuf;
     return FP_OK;
 }
 
@@ -497,8 +505,8 @@ static int predict_batched_chunk(const fp_device_forest *const *forests, const f
         if (bt.n == 0 || (!bt.out_votes && !bt.out_class)) continue;
         const FpImageHeader &h = f->hdr;
         int R = f->R;
-        while (R > 32 && smem_bytes(R, h.n_features, f->head_smem, h.n_classes, warps, false) > budget) R -= 32;
-        const size_t need = smem_bytes(R, h.n_features, f->head_smem, h.n_classes, warps, false);
+        while (R > 32 && smem_bytes(R, h.n_features, f->head_smem, f->nbuf, h.n_classes, warps, false) > budget) R -= 32;
+        const size_t need = smem_bytes(R, h.n_features, f->head_smem, f->nbuf, h.n_classes, warps, false);
         if (need > budget) {
             fp_set_error("fp_predict_batched: batch %d does not fit shared memory with %d warps", j, warps);
             return FP_EUNSUPPORTED;

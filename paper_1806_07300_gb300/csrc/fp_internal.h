@@ -98,6 +98,7 @@ struct FpImageHeader {
     int32_t obs_tile, warps_per_cta;
     int32_t max_head_bytes;
     int32_t refill_lanes;
+    int32_t bin_buffers;           // shared-memory buffers of the bin-block pipeline (2 or 3)
     int64_t n_super;               // super-nodes in the deep section
     int64_t off_bins, off_passes, off_tree_base, off_heads, off_deep;
     int64_t off_pheads, off_deep_leaf;

@@ -321,7 +321,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         fp_set_error("fp_pack_forest: tree_node_begin[0] must be 0");
         return FP_EINVAL;
     }
-    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0};
+    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0, 0, 0};
     const int32_t refill = p.refill_lanes ? p.refill_lanes : 32;
     int32_t B = p.bin_size ? p.bin_size : 1;
     const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
@@ -336,9 +336,11 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
     if (B < 1 || B > 1024 || d < 0 || d > (select_levels ? FP_MAX_LEVEL_DEPTH : FP_MAX_DEPTH) || W < 1 || W > 32 ||
         R < 32 || R > 2048 || R % 32 ||
-        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 1) {
+        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 1 ||
+        (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) || p.reserved != 0) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
-                     "refill %d, head_select %d)", B, d, R, W, refill, p.head_select);
+                     "refill %d, head_select %d, bin_buffers %d)", B, d, R, W, refill, p.head_select,
+                     p.bin_buffers);
         return FP_EINVAL;
     }
     if (B > T) B = T;
@@ -378,6 +380,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.head_select = select_levels ? 1 : 0;
         h.obs_tile = R; h.warps_per_cta = W;
         h.refill_lanes = refill;
+        h.bin_buffers = p.bin_buffers ? p.bin_buffers : 3;
         std::vector<FpBin> bins((size_t)n_bins);
         int64_t head_total = 0, phead_total = 0;
         int32_t max_head = 0;
@@ -581,6 +584,7 @@ void fp_fill_info(const FpImageHeader *h, fp_packed_info *info) {
     info->max_head_bytes = h->max_head_bytes;
     info->passes = h->n_passes;
     info->refill_lanes = h->refill_lanes;
+    info->bin_buffers = h->bin_buffers;
 }
 
 extern "C" const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes) {

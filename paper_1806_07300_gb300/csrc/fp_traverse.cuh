@@ -5,14 +5,15 @@
 // resident in L2 while every tile of observations goes through them (the GPU
 // counterpart of the paper's bins bound to cores, Section III).  For an item
 // the CTA:
-//   1. stages the tile's rows into shared memory with 4-byte cp.async,
-//      feature-major (x[f * R + r]), so 32 lanes holding 32 consecutive rows
-//      read any features from 32 different banks;
+//   1. stages the tile's rows into shared memory feature-major
+//      (x[f * R + r]), so 32 lanes holding 32 consecutive rows read any
+//      features from 32 different banks (16-byte loads along a row when the
+//      feature count is a multiple of 4, else 4-byte cp.async);
 //   2. streams the bins' interleaved blocks (the heads of their trees,
-//      Section III-A Bin) through FP_NBUF shared-memory buffers with TMA bulk
+//      Section III-A Bin) through nbuf (2 or 3) shared-memory buffers with TMA bulk
 //      copies (cp.async.bulk) completing on mbarriers: a warp waits only for
 //      the block of the bin it is about to claim, and the last warp to finish
-//      claiming a bin refills that buffer with the bin FP_NBUF places ahead;
+//      claiming a bin refills that buffer with the bin nbuf places ahead;
 //   3. walks (observation, tree) tasks in two kinds of warp steps:
 //        burst -- the warp claims 32 consecutive tasks (32 rows of one tree)
 //                 and all lanes walk their paths through the tree's head in
@@ -64,6 +65,7 @@ struct TravParams {
     int32_t F, C, T, R;
     int32_t n_passes;
     int32_t head_smem;        // bytes reserved for one bin block
+    int32_t nbuf;             // bin-block buffers (2 or 3)
     int32_t levels;           // 1: level heads (implicit slots, depth+1 steps); 0: ranked heads
     int32_t depth;            // d of the interleaved head
     int32_t refill;           // bursts start when the ring holds at most this many tasks
@@ -79,7 +81,7 @@ struct TravParams {
 
 #define FP_ERR_FLAG_DEVICE (-6)
 #define FP_ERR_FLAG_TIMEOUT (-5)
-#define FP_NBUF 3             // bin-block buffers in flight
+#define FP_NBUF 3             // bin-block buffers at most (a launch uses nbuf = 2 or 3)
 #define FP_SPIN_LIMIT (1 << 24)
 #define FP_RING 64            // pending tasks per warp
 #define FP_NO_CLASS (FP_REF_LEAF | 0x7FFFFFFFu)
@@ -220,6 +222,7 @@ struct CtaShared {
     int task_next[FP_NBUF];   // next unclaimed task of the buffer's bin
     int claim_done[FP_NBUF];  // warps done claiming the buffer's bin
     int issued[FP_NBUF];      // bulk copies issued into the buffer
+    int use0[FP_NBUF];        // issued[] when the current item started
     int last;
     int abort;
     long long next_item;
@@ -250,24 +253,27 @@ __device__ __forceinline__ void cta_finish(CtaShared &sh) {
     }
 }
 
-// One work item (pass, observation tile) of one forest.  seq_base counts the
-// bins this CTA has staged before the item; every thread tracks it alike.
+// One work item (pass, observation tile) of one forest.  Bin bi of the item
+// goes through buffer bi % nbuf; the k-th copy ever issued into a buffer
+// completes its barrier's phase k, so a wait needs the buffer's copy count
+// at the item's start (use0) plus bi / nbuf.  Counting per buffer keeps the
+// phases right when items of forests with different nbuf share a CTA.
 template <bool LEAVES>
-__device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh,
-                                         uint32_t &seq_base) {
+__device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
     const int R = p.R, F = p.F, C = p.C;
     float *xs = reinterpret_cast<float *>(smem);
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
-    uint8_t *const hbuf0 = smem + xs_bytes;  // FP_NBUF bin-block buffers, head_smem bytes each
-    uint32_t *svotes = reinterpret_cast<uint32_t *>(smem + xs_bytes + FP_NBUF * p.head_smem);
+    const int nbuf = p.nbuf;
+    uint8_t *const hbuf0 = smem + xs_bytes;  // nbuf bin-block buffers, head_smem bytes each
+    uint32_t *svotes = reinterpret_cast<uint32_t *>(smem + xs_bytes + nbuf * p.head_smem);
     const int vote_bytes = LEAVES ? 0 : ((R * C * 4) + 15) & ~15;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    uint2 *ring = reinterpret_cast<uint2 *>(smem + xs_bytes + FP_NBUF * p.head_smem + vote_bytes) + warp * FP_RING;
+    uint2 *ring = reinterpret_cast<uint2 *>(smem + xs_bytes + nbuf * p.head_smem + vote_bytes) + warp * FP_RING;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // one thread: stage bin b as the CTA's seq-th bin
-    auto issue = [&](int b, uint32_t seq) {
-        const int buf = (int)(seq % FP_NBUF);
+    // one thread: stage bin b of the pass, the item's bi-th bin
+    auto issue = [&](int b, int bi) {
+        const int buf = bi % nbuf;
         sh.task_next[buf] = 0;
         sh.claim_done[buf] = 0;
         sh.issued[buf] += 1;
@@ -293,15 +299,53 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
     {
         const float *src = p.X + row0 * F;
-        const int total = rows * F;
-        for (int e = tid; e < total; e += blockDim.x) {
-            const int r = e / F;
-            cp_async4(xs + (e - r * F) * R + r, src + e);
+        if ((F & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0) {
+            // lane = row: 16-byte loads along the row, and each store of a
+            // warp writes 32 consecutive rows of one feature (32 banks)
+            const int nq = F >> 2;
+            for (int g = warp; g * 32 < rows; g += nwarps) {
+                const int r = g * 32 + lane;
+                if (r < rows) {
+                    const float4 *rp = reinterpret_cast<const float4 *>(src + (int64_t)r * F);
+                    float *dst = xs + r;
+                    int q = 0;
+                    for (; q + 4 <= nq; q += 4) {
+                        float4 v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[u] = __ldg(rp + q + u);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float *d = dst + (4 * (q + u)) * R;
+                            d[0] = v[u].x;
+                            d[R] = v[u].y;
+                            d[2 * R] = v[u].z;
+                            d[3 * R] = v[u].w;
+                        }
+                    }
+                    for (; q < nq; ++q) {
+                        const float4 v = __ldg(rp + q);
+                        float *d = dst + (4 * q) * R;
+                        d[0] = v.x;
+                        d[R] = v.y;
+                        d[2 * R] = v.z;
+                        d[3 * R] = v.w;
+                    }
+                }
+            }
+        } else {
+            const int total = rows * F;
+            for (int e = tid; e < total; e += blockDim.x) {
+                const int r = e / F;
+                cp_async4(xs + (e - r * F) * R + r, src + e);
+            }
         }
         cp_async_commit();
     }
-    if (tid == 0 && !sh.abort)
-        for (int i = 0; i < FP_NBUF && i < nbins; ++i) issue(ps.bin_begin + i, seq_base + i);
+    if (tid == 0) {
+        for (int i = 0; i < FP_NBUF; ++i) sh.use0[i] = sh.issued[i];
+        if (!sh.abort)
+            for (int i = 0; i < nbuf && i < nbins; ++i) issue(ps.bin_begin + i, i);
+    }
     if (!LEAVES)
         for (int i = tid; i < rows * C; i += blockDim.x) svotes[i] = 0;
     cp_async_wait_all();
@@ -314,11 +358,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     L.ref = 0;
     int head = 0, tail = 0;  // warp-uniform ring cursors
 
+    const int u0 = sh.use0[0], u1 = sh.use0[1], u2 = sh.use0[2];  // read after the barrier above
     for (int bi = 0; bi < nbins; ++bi) {
-        const uint32_t seq = seq_base + bi;
-        const int buf = (int)(seq % FP_NBUF);
+        const int buf = bi % nbuf;
         {  // wait until the bin's block has landed
-            const uint32_t parity = (seq / FP_NBUF) & 1u;
+            const int ub = buf == 0 ? u0 : (buf == 1 ? u1 : u2);
+            const uint32_t parity = (uint32_t)(ub + bi / nbuf) & 1u;
             bool ok = false;
             for (int spin = 0; spin < p.spin_limit; ++spin) {
                 if (*(volatile int *)&sh.abort) break;
@@ -415,12 +460,11 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         __syncwarp();
         if (lane == 0) {
             const int done = atomicAdd(&sh.claim_done[buf], 1);
-            if (done == nwarps - 1 && bi + FP_NBUF < nbins && !*(volatile int *)&sh.abort)
-                issue(ps.bin_begin + bi + FP_NBUF, seq + FP_NBUF);
+            if (done == nwarps - 1 && bi + nbuf < nbins && !*(volatile int *)&sh.abort)
+                issue(ps.bin_begin + bi + nbuf, bi + nbuf);
         }
         __syncwarp();
     }
-    seq_base += (uint32_t)nbins;
     const bool aborted = *(volatile int *)&sh.abort != 0;
     // drain: the item's last pending and running tasks
     for (; !aborted;) {
@@ -491,8 +535,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 1024 : 512, MINB) fp_traverse_kern
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    uint32_t seq_base = 0;
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<LEAVES>(p, item, smem, sh, seq_base);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<LEAVES>(p, item, smem, sh);
     cta_finish(sh);
 }
 
@@ -512,7 +555,6 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    uint32_t seq_base = 0;
     const int64_t total = bp.item_begin[bp.k];
     for (;;) {
         if (threadIdx.x == 0) sh.next_item = (long long)atomicAdd(bp.work, 1ull);
@@ -522,7 +564,7 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         if (item >= total) break;
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
-        run_item<false>(bp.p[j], item - bp.item_begin[j], smem, sh, seq_base);
+        run_item<false>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }

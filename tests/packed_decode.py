@@ -8,7 +8,7 @@ import numpy as np
 HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_trees", "<i4"), ("n_features", "<i4"),
                 ("n_classes", "<i4"), ("bin_size", "<i4"), ("depth", "<i4"), ("n_bins", "<i4"),
                 ("n_passes", "<i4"), ("head_nodes", "<i4"), ("head_select", "<i4"), ("obs_tile", "<i4"),
-                ("warps_per_cta", "<i4"), ("max_head_bytes", "<i4"), ("refill_lanes", "<i4"), ("n_super", "<i8"),
+                ("warps_per_cta", "<i4"), ("max_head_bytes", "<i4"), ("refill_lanes", "<i4"), ("bin_buffers", "<i4"), ("n_super", "<i8"),
                 ("off_bins", "<i8"), ("off_passes", "<i8"), ("off_tree_base", "<i8"), ("off_heads", "<i8"),
                 ("off_deep", "<i8"), ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"),
                 ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8")],

@@ -26,9 +26,9 @@ def test_candidate_layouts_pack(tiny_forest):
 
 
 def test_candidate_launches():
-    for tile, warps, refill in at.candidate_launches(480):
+    for tile, warps, refill, nbuf in at.candidate_launches(480):
         assert tile % 32 == 0 and 32 <= tile <= 480
-        assert warps in (16, 32) and refill in (16, 32)
+        assert warps in (16, 32) and refill in (16, 32) and nbuf in (2, 3)
 
 
 def test_forest_key_changes_with_forest(tiny_forest):
@@ -49,7 +49,7 @@ def test_autotune_tiny_on_gpu(tiny_forest, tiny_rows, tmp_path, monkeypatch):
     X, _ = tiny_rows
     Xd = torch.from_numpy(X).cuda()
     best = at.autotune(tiny_forest, Xd, layouts=[(1, 3), (16, 4, 1), (4, 6, 0), (2, 7, 1)],
-                       launches=[(256, 16, 16), (128, 32, 32)])
+                       launches=[(256, 16, 16), (128, 32, 32, 2)])
     assert best["ms"] > 0 and len(best["table"]) == 8
     again = at.autotune(tiny_forest, Xd, layouts=[(1, 0)])  # served from the cache
     assert all(again[k] == best[k] for k in at.LAYOUT_KEYS)

@@ -37,13 +37,17 @@ def _check(forest_objs, Xh, votes, cls, sample=None):
 
 
 def test_batched_mixed_layouts_and_passes(tiny_forest, tiny_rows):
-    """One launch over forests with different bins, heads and pass counts."""
+    """One launch over forests with different bins, heads, pass counts and
+    bin-buffer counts (items of forests streaming through two and three
+    buffers share CTAs)."""
     X, _ = tiny_rows
     params = [dict(bin_size=1, interleave_depth=0), dict(bin_size=4, interleave_depth=3),
               dict(bin_size=2, interleave_depth=1, pass_bytes=2048), dict(bin_size=16, interleave_depth=9),
-              dict(bin_size=3, interleave_depth=5, pass_bytes=1), dict(bin_size=8, interleave_depth=4, head_select=1),
-              dict(bin_size=2, interleave_depth=6, head_select=1, pass_bytes=4096)]
-    sizes = [1, 777, 31, 4096, 2500, 1500, 999]
+              dict(bin_size=3, interleave_depth=5, pass_bytes=1),
+              dict(bin_size=8, interleave_depth=4, head_select=1, bin_buffers=2),
+              dict(bin_size=2, interleave_depth=6, head_select=1, pass_bytes=4096, bin_buffers=2),
+              dict(bin_size=3, interleave_depth=3, pass_bytes=2048, bin_buffers=2)]
+    sizes = [1, 777, 31, 4096, 2500, 1500, 999, 3333]
     forests = [fp.fp_upload(fp.fp_pack_forest(tiny_forest, **p)) for p in params]
     Xh = [X[i * 7: i * 7 + n] for i, n in enumerate(sizes)]
     Xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in Xh]

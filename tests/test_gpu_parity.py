@@ -72,6 +72,15 @@ def test_tiny_tiles_and_ragged_tail(tiny_forest, tiny_rows, tile, warps):
     _check_all(tiny_forest, X[:tile * 3 + 17], bin_size=4, interleave_depth=2, obs_tile=tile, warps_per_cta=warps)
 
 
+@pytest.mark.parametrize("B,d,sel,nbuf", [(1, 9, 1, 2), (4, 5, 1, 2), (3, 7, 0, 2), (2, 3, 1, 3)])
+def test_tiny_two_bin_buffers(tiny_forest, tiny_rows, B, d, sel, nbuf):
+    """Bin blocks streamed through two (or three) shared-memory buffers."""
+    X, _ = tiny_rows
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, bin_buffers=nbuf)
+    _check_all(tiny_forest, X[:777], bin_size=B, interleave_depth=d, head_select=sel, bin_buffers=nbuf,
+               pass_bytes=4096, obs_tile=64)
+
+
 @pytest.mark.parametrize("pass_bytes", [1, 2048, 8192])
 @pytest.mark.parametrize("sel", [0, 1])
 def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes, sel):

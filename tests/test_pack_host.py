@@ -221,6 +221,8 @@ def test_pack_info_sizes(tiny_forest):
     assert info["n_internal"] == int((tiny_forest.left >= 0).sum())
     assert info["deep_bytes"] == 32 * info["n_super"]
     assert info["n_bins"] == 1 and info["passes"] == 1
+    assert info["bin_buffers"] == 3
+    assert fp.fp_pack_forest(tiny_forest, bin_buffers=2).info()["bin_buffers"] == 2
 
 
 def test_passes_split_by_budget(tiny_forest):
@@ -267,7 +269,8 @@ def test_unsupported_sizes_rejected():
 
 
 @pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(interleave_depth=12, head_select=1),
-                                dict(obs_tile=33), dict(warps_per_cta=40), dict(head_select=2)])
+                                dict(obs_tile=33), dict(warps_per_cta=40), dict(head_select=2),
+                                dict(bin_buffers=1), dict(bin_buffers=4)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(tiny_forest, **kw)
