@@ -19,6 +19,13 @@ Workloads (each a dict made by :func:`workload`):
 * ``batched``: 8 Gaussian-mixture forests of varied tree, feature and class
   counts; seed 4.
 * ``wide``: 64-tree, 50-class, 100-feature mixture forest for serving; seed 5.
+* ``regress``: regression forest with real leaf values (the forest variants
+  the paper names beside classification): the ``hbm`` features with a real
+  target (the logistic model's score plus Gaussian noise); 200,000 training
+  rows, 128 trees, mtry 9, leaves of at least 5; seed 6.
+* ``boosted``: gradient-boosted shallow trees (squared loss, depth <= 6,
+  learning rate 0.1) on the same kind of rows; 30,000 training rows, 256
+  rounds; seed 7.
 """
 from __future__ import annotations
 
@@ -88,6 +95,12 @@ def lib():
             L.dg_stream_first.restype = u64
             L.dg_xoshiro_from_state.argtypes = [P, ctypes.c_int, P]
             L.dg_xoshiro_from_state.restype = None
+            L.dg_gen_regression.argtypes = [u64, i64, u32, dbl, dbl, P, P, ctypes.c_int]
+            L.dg_gen_regression.restype = ctypes.c_int
+            L.dg_train_regression.argtypes = [P, P, i64, i32, i32, i32, i32, i64, dbl, u64, P, ctypes.c_int]
+            L.dg_train_regression.restype = P
+            L.dg_forest_export_values.argtypes = [P, P]
+            L.dg_forest_export_values.restype = None
             _lib = L
     return _lib
 
@@ -131,6 +144,15 @@ def gen_logistic(seed: int, n: int, split: int, scale: float = HBM_LOGIT_SCALE):
     return X, y
 
 
+def gen_regression(seed: int, n: int, split: int, scale: float = 1.0, noise: float = 1.0):
+    X = np.empty((n, 28), dtype=np.float32)
+    y = np.empty(n, dtype=np.float64)
+    rc = lib().dg_gen_regression(seed, n, split, scale, noise, _ptr(X), _ptr(y), n_threads())
+    if rc != 0:
+        raise RuntimeError(f"dg_gen_regression failed: {rc}")
+    return X, y
+
+
 # --------------------------------------------------------------- forests
 
 class Forest:
@@ -138,11 +160,13 @@ class Forest:
 
     ``left[i] == -1`` marks a leaf; ``leaf_class`` is set on leaves only.
     ``cardinality`` is the in-bag training count (with bootstrap multiplicity)
-    reaching each node.
+    reaching each node.  Forests with real leaf values (regression, boosting)
+    also carry ``leaf_value`` (float32 per node, 0 on internal nodes) and
+    predict ``value_bias + value_scale * sum over trees of the leaf value``.
     """
 
     def __init__(self, n_features, n_classes, node_begin, left, right, feature, threshold,
-                 leaf_class, cardinality, tree_depth=None):
+                 leaf_class, cardinality, tree_depth=None, leaf_value=None, value_scale=1.0, value_bias=0.0):
         self.n_features = int(n_features)
         self.n_classes = int(n_classes)
         self.node_begin = np.ascontiguousarray(node_begin, dtype=np.int64)
@@ -155,6 +179,9 @@ class Forest:
         if tree_depth is None:
             tree_depth = np.zeros(self.n_trees, dtype=np.int32)
         self.tree_depth = np.ascontiguousarray(tree_depth, dtype=np.int32)
+        self.leaf_value = None if leaf_value is None else np.ascontiguousarray(leaf_value, dtype=np.float32)
+        self.value_scale = float(value_scale)
+        self.value_bias = float(value_bias)
 
     @property
     def n_trees(self) -> int:
@@ -181,15 +208,22 @@ class Forest:
         os.makedirs(path, exist_ok=True)
         for k in self._FIELDS:
             np.save(os.path.join(path, k + ".npy"), getattr(self, k))
+        if self.leaf_value is not None:
+            np.save(os.path.join(path, "leaf_value.npy"), self.leaf_value)
         with open(os.path.join(path, "meta.json"), "w") as f:
-            json.dump({"n_features": self.n_features, "n_classes": self.n_classes}, f)
+            json.dump({"n_features": self.n_features, "n_classes": self.n_classes,
+                       "value_scale": self.value_scale, "value_bias": self.value_bias}, f)
 
     @classmethod
     def load(cls, path: str) -> "Forest":
         with open(os.path.join(path, "meta.json")) as f:
             meta = json.load(f)
         arrs = {k: np.load(os.path.join(path, k + ".npy")) for k in cls._FIELDS}
-        return cls(meta["n_features"], meta["n_classes"], **arrs)
+        lv = os.path.join(path, "leaf_value.npy")
+        if os.path.exists(lv):
+            arrs["leaf_value"] = np.load(lv)
+        return cls(meta["n_features"], meta["n_classes"], value_scale=meta.get("value_scale", 1.0),
+                   value_bias=meta.get("value_bias", 0.0), **arrs)
 
 
 def train_forest(X: np.ndarray, y: np.ndarray, n_classes: int, n_trees: int, mtry: int | None = None,
@@ -222,6 +256,43 @@ def train_forest(X: np.ndarray, y: np.ndarray, n_classes: int, n_trees: int, mtr
     return Forest(d, n_classes, node_begin, left, right, feature, threshold, leaf_class, card, depth)
 
 
+def train_regression(X: np.ndarray, y: np.ndarray, n_trees: int, mtry: int | None = None, max_depth: int = 0,
+                     min_leaf: int = 1, eta: float = 0.0, seed: int = 0, threads: int | None = None) -> Forest:
+    """A regression forest (eta == 0: bootstrap, mean of the trees) or a
+    boosted ensemble (eta > 0: F_0 + sum of the trees); see datagen.c."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n, d = X.shape
+    if mtry is None:
+        mtry = max(1, d // 3)
+    L = lib()
+    base = ctypes.c_double(0.0)
+    h = L.dg_train_regression(_ptr(X), _ptr(y), n, d, n_trees, mtry, max_depth, min_leaf, eta, seed,
+                              ctypes.addressof(base), threads or n_threads())
+    if not h:
+        raise RuntimeError("dg_train_regression failed (bad arguments or out of memory)")
+    try:
+        T = L.dg_forest_n_trees(h)
+        m = L.dg_forest_total_nodes(h)
+        node_begin = np.empty(T + 1, np.int64)
+        left = np.empty(m, np.int32)
+        right = np.empty(m, np.int32)
+        feature = np.empty(m, np.int32)
+        threshold = np.empty(m, np.float32)
+        leaf_class = np.empty(m, np.int32)
+        card = np.empty(m, np.int64)
+        depth = np.empty(T, np.int32)
+        value = np.empty(m, np.float32)
+        L.dg_forest_export(h, _ptr(node_begin), _ptr(left), _ptr(right), _ptr(feature), _ptr(threshold),
+                           _ptr(leaf_class), _ptr(card), _ptr(depth))
+        L.dg_forest_export_values(h, _ptr(value))
+    finally:
+        L.dg_forest_free(h)
+    scale = 1.0 / T if eta == 0.0 else 1.0
+    return Forest(d, 1, node_begin, left, right, feature, threshold, leaf_class, card, depth,
+                  leaf_value=value, value_scale=scale, value_bias=base.value)
+
+
 def bootstrap_weights(seed: int, tree: int, n: int) -> np.ndarray:
     w = np.empty(n, np.int64)
     lib().dg_bootstrap_weights(seed, tree, n, _ptr(w))
@@ -246,6 +317,10 @@ RECIPES = {
     "hbm": dict(kind="logistic", seed=3, C=2, d=28, n_train=500000, n_test=4000000, T=256, mtry=5,
                 scale=HBM_LOGIT_SCALE),
     "wide": dict(kind="mixture", seed=5, C=50, d=100, n_train=50000, n_test=100000, T=64, mtry=10),
+    "regress": dict(kind="regression", seed=6, C=1, d=28, n_train=200000, n_test=4000000, T=128, mtry=9,
+                    max_depth=0, min_leaf=5, eta=0.0, noise=1.0),
+    "boosted": dict(kind="regression", seed=7, C=1, d=28, n_train=30000, n_test=4000000, T=256, mtry=28,
+                    max_depth=6, min_leaf=1, eta=0.1, noise=1.0),
 }
 for _k, (_T, _d, _C) in enumerate(BATCHED_SPECS):
     RECIPES[f"batched{_k}"] = dict(kind="mixture", seed=400 + _k, C=_C, d=_d, n_train=_batched_train_rows(_k),
@@ -270,6 +345,8 @@ def rows(name: str, split: int, n: int | None = None):
         return gen_image(r["seed"], n, split)
     if r["kind"] == "logistic":
         return gen_logistic(r["seed"], n, split, r["scale"])
+    if r["kind"] == "regression":
+        return gen_regression(r["seed"], n, split, 1.0, r["noise"])
     raise KeyError(r["kind"])
 
 
@@ -280,7 +357,11 @@ def forest(name: str, use_cache: bool = True) -> Forest:
     if use_cache and os.path.exists(os.path.join(path, "meta.json")):
         return Forest.load(path)
     X, y = rows(name, 0)
-    F = train_forest(X, y, r["C"], r["T"], r["mtry"], seed=r["seed"])
+    if r["kind"] == "regression":
+        F = train_regression(X, y, r["T"], r["mtry"], max_depth=r["max_depth"], min_leaf=r["min_leaf"],
+                             eta=r["eta"], seed=r["seed"])
+    else:
+        F = train_forest(X, y, r["C"], r["T"], r["mtry"], seed=r["seed"])
     if use_cache:
         tmp = path + f".tmp{os.getpid()}"
         F.save(tmp)

@@ -245,7 +245,7 @@ int dg_gen_image(uint64_t seed, int64_t n, uint32_t split, float *X, int32_t *y,
 #define LOG_NNORM 21
 #define LOG_PAIRS 28
 
-typedef struct { uint64_t seed; int64_t n; uint32_t split; double s; double w[LOG_D]; int pi[LOG_PAIRS], pj[LOG_PAIRS]; double v[LOG_PAIRS]; float *X; int32_t *y; } log_ctx;
+typedef struct { uint64_t seed; int64_t n; uint32_t split; double s; double w[LOG_D]; int pi[LOG_PAIRS], pj[LOG_PAIRS]; double v[LOG_PAIRS]; float *X; int32_t *y; double *yr; double noise; } log_ctx;
 
 static void log_chunk(void *vc, int64_t chunk) {
     log_ctx *c = (log_ctx *)vc;
@@ -262,15 +262,20 @@ static void log_chunk(void *vc, int64_t chunk) {
             logit += c->w[f] * z[f];
         }
         for (int q = 0; q < LOG_PAIRS; ++q) logit += c->v[q] * z[c->pi[q]] * z[c->pj[q]];
+        if (c->yr) {  /* regression target: the score plus Gaussian noise */
+            c->yr[i] = c->s * logit + c->noise * dg_normal(&r);
+            continue;
+        }
         double p = 1.0 / (1.0 + exp(-c->s * logit));
         c->y[i] = dg_uniform(&r) < p ? 1 : 0;
     }
 }
 
-int dg_gen_logistic(uint64_t seed, int64_t n, uint32_t split, double scale, float *X, int32_t *y, int n_threads) {
+static int gen_logistic_like(uint64_t seed, int64_t n, uint32_t split, double scale, float *X, int32_t *y,
+                             double *yr, double noise, int n_threads) {
     log_ctx *c = (log_ctx *)calloc(1, sizeof(log_ctx));
     if (!c) return -2;
-    c->seed = seed; c->n = n; c->split = split; c->s = scale; c->X = X; c->y = y;
+    c->seed = seed; c->n = n; c->split = split; c->s = scale; c->X = X; c->y = y; c->yr = yr; c->noise = noise;
     dg_rng r;
     dg_rng_init(&r, seed, PURPOSE_PARAMS, 0);
     for (int f = 0; f < LOG_D; ++f) c->w[f] = dg_normal(&r) * sqrt(1.0 / LOG_D);
@@ -286,11 +291,23 @@ int dg_gen_logistic(uint64_t seed, int64_t n, uint32_t split, double scale, floa
     return 0;
 }
 
+int dg_gen_logistic(uint64_t seed, int64_t n, uint32_t split, double scale, float *X, int32_t *y, int n_threads) {
+    return gen_logistic_like(seed, n, split, scale, X, y, NULL, 0.0, n_threads);
+}
+
+/* Regression rows: the features of the logistic generator and a real target
+ * y = scale * (w.z + sum v_ij z_i z_j) + noise * N(0, 1). */
+int dg_gen_regression(uint64_t seed, int64_t n, uint32_t split, double scale, double noise, float *X, double *y,
+                      int n_threads) {
+    return gen_logistic_like(seed, n, split, scale, X, NULL, y, noise, n_threads);
+}
+
 /* --------------------------------------------------------------- trainer */
 
 typedef struct {
     int32_t *left, *right, *feature, *leaf_class;
     float *threshold;
+    float *value;             /* leaf value (regression and boosted trees; 0 elsewhere) */
     int64_t *card;
     int64_t n_nodes, cap;
     int32_t depth;            /* maximum node depth (root = 0) */
@@ -378,6 +395,7 @@ static int64_t tree_push(dg_tree *t) {
         r2 = realloc(t->feature, sizeof(int32_t) * nc); if (!r2) { t->oom = 1; return -1; } t->feature = r2;
         r2 = realloc(t->leaf_class, sizeof(int32_t) * nc); if (!r2) { t->oom = 1; return -1; } t->leaf_class = r2;
         float *th = realloc(t->threshold, sizeof(float) * nc); if (!th) { t->oom = 1; return -1; } t->threshold = th;
+        th = realloc(t->value, sizeof(float) * nc); if (!th) { t->oom = 1; return -1; } t->value = th;
         int64_t *cd = realloc(t->card, sizeof(int64_t) * nc); if (!cd) { t->oom = 1; return -1; } t->card = cd;
         t->cap = nc;
     }
@@ -458,6 +476,7 @@ static int64_t grow(const train_ctx *c, tree_ws *ws, dg_tree *t, int64_t lo, int
         if (cnt[k] > cnt[maj]) maj = k;
     }
     t->left[id] = -1; t->right[id] = -1; t->feature[id] = -1; t->threshold[id] = 0.0f; t->leaf_class[id] = maj;
+    t->value[id] = 0.0f;
     if (nz <= 1) return id;
 
     /* feature draws: partial Fisher-Yates, continued until a feature splits */
@@ -550,6 +569,7 @@ void dg_forest_free(dg_forest *F) {
     for (int32_t t = 0; t < F->n_trees; ++t) {
         dg_tree *tr = &F->trees[t];
         free(tr->left); free(tr->right); free(tr->feature); free(tr->leaf_class); free(tr->threshold); free(tr->card);
+        free(tr->value);
     }
     free(F->trees);
     free(F);
@@ -612,4 +632,243 @@ void dg_bootstrap_weights(uint64_t seed, int32_t tree, int64_t n, int64_t *w) {
     dg_rng_init(&r, seed, PURPOSE_TREE, (uint64_t)tree);
     memset(w, 0, sizeof(int64_t) * (size_t)n);
     for (int64_t i = 0; i < n; ++i) w[dg_bounded(&r, (uint64_t)n)]++;
+}
+
+/* ------------------------------------------------------ regression trainer */
+/* Least-squares regression trees (CART) in two forest forms, for forests with
+ * real leaf values:
+ *   random forest (Breiman 2001): each tree on a bootstrap of the rows with
+ *     multiplicities as weights and mtry features per node (draws continued
+ *     as in the classifier); a node is a leaf when its targets are all equal,
+ *     when it holds less than 2*min_leaf weight, or at max_depth (0 = no
+ *     limit); leaf value = weighted mean of the node's targets; the forest
+ *     predicts the mean of its trees;
+ *   gradient boosting with squared loss (Friedman 2001): F_0 = mean(y); round
+ *     m fits a tree of depth <= max_depth to the residuals y - F_{m-1}(x) of
+ *     all rows (weight 1); leaf value = eta * mean residual; the forest
+ *     predicts F_0 + the sum of its trees.
+ * Split: maximise S_L^2/W_L + S_R^2/W_R (S = weighted target sum, W = weight;
+ * the squared-error decrease up to a constant) in double precision, samples
+ * accumulated in ascending feature order; both sides must hold weight >=
+ * min_leaf; ties keep the earlier feature in draw order, then the smaller
+ * threshold.  Thresholds as in the classifier.  A leaf value is rounded to
+ * float once; boosting adds that float value to the rows' running score. */
+
+typedef struct {
+    const float *X; const double *y; int64_t n; int32_t d, mtry, max_depth; int64_t min_leaf; uint64_t seed;
+    double eta; dg_forest *F;
+    const double *target;  /* what the current tree fits: y (forest) or the residuals (boosting) */
+    double *score;         /* boosting: F(x_i) of the training rows, updated at each leaf */
+} reg_ctx;
+
+typedef struct {
+    int32_t *samp, *tmp, *pay, *pay2, *perm;
+    int64_t *w;
+    uint32_t *key, *key2;
+    dg_rng rng;
+} reg_ws;
+
+static int reg_ws_alloc(reg_ws *ws, int64_t n, int32_t d) {
+    memset(ws, 0, sizeof *ws);
+    ws->samp = malloc(sizeof(int32_t) * (size_t)n);
+    ws->tmp = malloc(sizeof(int32_t) * (size_t)n);
+    ws->pay = malloc(sizeof(int32_t) * (size_t)n);
+    ws->pay2 = malloc(sizeof(int32_t) * (size_t)n);
+    ws->perm = malloc(sizeof(int32_t) * (size_t)d);
+    ws->w = malloc(sizeof(int64_t) * (size_t)n);
+    ws->key = malloc(sizeof(uint32_t) * (size_t)n);
+    ws->key2 = malloc(sizeof(uint32_t) * (size_t)n);
+    return ws->samp && ws->tmp && ws->pay && ws->pay2 && ws->perm && ws->w && ws->key && ws->key2;
+}
+
+static void reg_ws_free(reg_ws *ws) {
+    free(ws->samp); free(ws->tmp); free(ws->pay); free(ws->pay2); free(ws->perm); free(ws->w);
+    free(ws->key); free(ws->key2);
+}
+
+/* Best threshold of feature f on samp[lo:hi]; returns 1 if a split with both
+ * sides >= min_leaf exists. */
+static int best_split_reg(const reg_ctx *c, reg_ws *ws, int64_t lo, int64_t hi, int32_t f, double S, int64_t W,
+                          double *out_score, float *out_thr) {
+    const int64_t m = hi - lo;
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t s = ws->samp[lo + i];
+        ws->key[i] = float_key(c->X[(int64_t)s * c->d + f]);
+        ws->pay[i] = s;
+    }
+    sort_pairs(ws->key, ws->pay, ws->key2, ws->pay2, m);
+    if (ws->key[0] == ws->key[m - 1]) return 0;
+    double SL = 0.0, best = 0.0;
+    int64_t WL = 0;
+    int found = 0;
+    float bthr = 0.0f;
+    for (int64_t i = 0; i + 1 < m; ++i) {
+        int32_t s = ws->pay[i];
+        int64_t wi = ws->w[s];
+        SL += (double)wi * c->target[s];
+        WL += wi;
+        if (ws->key[i] == ws->key[i + 1]) continue;
+        const int64_t WR = W - WL;
+        if (WL < c->min_leaf || WR < c->min_leaf) continue;
+        const double SR = S - SL;
+        const double score = SL * SL / (double)WL + SR * SR / (double)WR;
+        if (!found || score > best) {
+            float a = key_float(ws->key[i]), b = key_float(ws->key[i + 1]);
+            float t = (float)((double)a + ((double)b - (double)a) * 0.5);
+            if (!(t >= a && t < b)) t = a;
+            best = score; bthr = t; found = 1;
+        }
+    }
+    *out_score = best; *out_thr = bthr;
+    return found;
+}
+
+static int64_t grow_reg(const reg_ctx *c, reg_ws *ws, dg_tree *t, int64_t lo, int64_t hi, int32_t depth) {
+    int64_t id = tree_push(t);
+    if (id < 0) return -1;
+    if (depth > t->depth) t->depth = depth;
+    const int32_t d = c->d;
+    int64_t W = 0;
+    double S = 0.0, ymin = 0.0, ymax = 0.0;
+    for (int64_t i = lo; i < hi; ++i) {
+        int32_t s = ws->samp[i];
+        const double v = c->target[s];
+        W += ws->w[s];
+        S += (double)ws->w[s] * v;
+        if (i == lo || v < ymin) ymin = v;
+        if (i == lo || v > ymax) ymax = v;
+    }
+    t->card[id] = W;
+    t->left[id] = -1; t->right[id] = -1; t->feature[id] = -1; t->threshold[id] = 0.0f; t->leaf_class[id] = 0;
+    t->value[id] = (float)((c->eta > 0.0 ? c->eta : 1.0) * (S / (double)W));
+    int32_t bf = -1;
+    double bscore = 0.0;
+    float bthr = 0.0f;
+    if (ymin != ymax && W >= 2 * c->min_leaf && !(c->max_depth > 0 && depth >= c->max_depth)) {
+        for (int32_t f = 0; f < d; ++f) ws->perm[f] = f;
+        for (int32_t i = 0; i < d; ++i) {
+            int32_t j = i + (int32_t)dg_bounded(&ws->rng, (uint64_t)(d - i));
+            int32_t tmpf = ws->perm[i]; ws->perm[i] = ws->perm[j]; ws->perm[j] = tmpf;
+            double score; float thr;
+            if (best_split_reg(c, ws, lo, hi, ws->perm[i], S, W, &score, &thr)) {
+                if (bf < 0 || score > bscore) { bf = ws->perm[i]; bscore = score; bthr = thr; }
+            }
+            if (i + 1 >= c->mtry && bf >= 0) break;
+        }
+    }
+    if (bf < 0) {  /* a leaf: boosting adds its value to the rows that reach it */
+        if (c->score)
+            for (int64_t i = lo; i < hi; ++i) c->score[ws->samp[i]] += (double)t->value[id];
+        return id;
+    }
+    int64_t nl = 0;
+    for (int64_t i = lo; i < hi; ++i) {
+        int32_t s = ws->samp[i];
+        if (c->X[(int64_t)s * d + bf] <= bthr) ws->samp[lo + nl++] = s; else ws->tmp[i - lo - nl] = s;
+    }
+    memcpy(ws->samp + lo + nl, ws->tmp, sizeof(int32_t) * (size_t)(hi - lo - nl));
+    t->feature[id] = bf;
+    t->threshold[id] = bthr;
+    t->leaf_class[id] = -1;
+    t->value[id] = 0.0f;
+    int64_t l = grow_reg(c, ws, t, lo, lo + nl, depth + 1);
+    if (l < 0) return -1;
+    int64_t r = grow_reg(c, ws, t, lo + nl, hi, depth + 1);
+    if (r < 0) return -1;
+    t->left[id] = (int32_t)l;
+    t->right[id] = (int32_t)r;
+    return id;
+}
+
+typedef struct { reg_ctx *c; int64_t next; pthread_mutex_t mu; int fail; } reg_pool;
+
+static void *reg_forest_worker(void *arg) {
+    reg_pool *p = (reg_pool *)arg;
+    reg_ctx *c = p->c;
+    reg_ws ws;
+    int ok = reg_ws_alloc(&ws, c->n, c->d);
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        int64_t ti = p->next++;
+        if (!ok) p->fail = 1;
+        pthread_mutex_unlock(&p->mu);
+        if (!ok || ti >= c->F->n_trees) break;
+        dg_tree *t = &c->F->trees[ti];
+        dg_rng_init(&ws.rng, c->seed, PURPOSE_TREE, (uint64_t)ti);
+        memset(ws.w, 0, sizeof(int64_t) * (size_t)c->n);
+        for (int64_t i = 0; i < c->n; ++i) ws.w[dg_bounded(&ws.rng, (uint64_t)c->n)]++;
+        int64_t m = 0;
+        for (int64_t i = 0; i < c->n; ++i)
+            if (ws.w[i]) ws.samp[m++] = (int32_t)i;
+        t->n_boot = c->n;
+        if (grow_reg(c, &ws, t, 0, m, 0) < 0 || t->oom) {
+            pthread_mutex_lock(&p->mu); p->fail = 1; pthread_mutex_unlock(&p->mu);
+        }
+    }
+    reg_ws_free(&ws);
+    return NULL;
+}
+
+/* Train a regression forest (eta == 0) or a boosted ensemble (eta > 0).
+ * *base receives F_0 (boosting) or 0.  Returns NULL on bad arguments or
+ * allocation failure. */
+dg_forest *dg_train_regression(const float *X, const double *y, int64_t n, int32_t d, int32_t n_trees, int32_t mtry,
+                               int32_t max_depth, int64_t min_leaf, double eta, uint64_t seed, double *base,
+                               int n_threads) {
+    if (n < 2 || n > INT32_MAX || d < 1 || n_trees < 1 || mtry < 1 || max_depth < 0 || min_leaf < 1 || eta < 0.0 ||
+        !base)
+        return NULL;
+    dg_forest *F = calloc(1, sizeof(dg_forest));
+    if (!F) return NULL;
+    F->n_trees = n_trees; F->n_features = d; F->n_classes = 1;
+    F->trees = calloc((size_t)n_trees, sizeof(dg_tree));
+    if (!F->trees) { free(F); return NULL; }
+    reg_ctx c = {X, y, n, d, mtry > d ? d : mtry, max_depth, min_leaf, seed, eta, F, y, NULL};
+    *base = 0.0;
+    if (eta == 0.0) {
+        reg_pool p = {&c, 0, PTHREAD_MUTEX_INITIALIZER, 0};
+        if (n_threads < 1) n_threads = 1;
+        if (n_threads > n_trees) n_threads = n_trees;
+        if (n_threads > 256) n_threads = 256;
+        pthread_t th[256];
+        for (int i = 0; i < n_threads; ++i) pthread_create(&th[i], NULL, reg_forest_worker, &p);
+        for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+        if (p.fail) { dg_forest_free(F); return NULL; }
+        return F;
+    }
+    /* boosting: rounds are sequential */
+    reg_ws ws;
+    double *score = malloc(sizeof(double) * (size_t)n), *resid = malloc(sizeof(double) * (size_t)n);
+    int ok = reg_ws_alloc(&ws, n, d) && score && resid;
+    if (ok) {
+        double s0 = 0.0;
+        for (int64_t i = 0; i < n; ++i) s0 += y[i];
+        *base = s0 / (double)n;
+        for (int64_t i = 0; i < n; ++i) score[i] = *base;
+        for (int64_t i = 0; i < n; ++i) ws.w[i] = 1;
+        c.target = resid;
+        c.score = score;
+        for (int32_t m = 0; m < n_trees && ok; ++m) {
+            for (int64_t i = 0; i < n; ++i) resid[i] = y[i] - score[i];
+            for (int64_t i = 0; i < n; ++i) ws.samp[i] = (int32_t)i;
+            dg_rng_init(&ws.rng, seed, PURPOSE_TREE, (uint64_t)m);
+            dg_tree *t = &F->trees[m];
+            t->n_boot = n;
+            if (grow_reg(&c, &ws, t, 0, n, 0) < 0 || t->oom) ok = 0;
+        }
+    }
+    reg_ws_free(&ws);
+    free(score); free(resid);
+    if (!ok) { dg_forest_free(F); return NULL; }
+    return F;
+}
+
+/* Leaf values of every node (0 on internal nodes), in export order. */
+void dg_forest_export_values(const dg_forest *F, float *value) {
+    int64_t off = 0;
+    for (int32_t t = 0; t < F->n_trees; ++t) {
+        const dg_tree *tr = &F->trees[t];
+        memcpy(value + off, tr->value, 4 * (size_t)tr->n_nodes);
+        off += tr->n_nodes;
+    }
 }

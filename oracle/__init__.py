@@ -2,7 +2,10 @@
 
 A plain, slow, obviously correct C implementation of forest classification
 (Section III of the paper) and of the paper's own layouts (Section III-A:
-BF, DF, DF-, Stat, Bin; Section III-B: Bin+ round-robin evaluation).  Only the
+BF, DF, DF-, Stat, Bin; Section III-B: Bin+ round-robin evaluation), and the
+plain definition of forests with real leaf values (regression and boosted
+trees, the other forest variants the paper names): the leaf walk above, then
+bias + scale * the fp64 sum of the reached leaves' values.  Only the
 tests, the smoke check and the benchmark's CPU-baseline leg may use it; the
 GPU library never imports it and shares no code with it.
 """
@@ -96,6 +99,35 @@ def predict(forest, X: np.ndarray, leaves: bool = True, votes: bool = True, clas
     if rc != 0:
         raise RuntimeError(f"or_predict failed: {rc}")
     return dict(leaf=out_leaf, votes=out_votes, cls=out_cls, visits=int(visits.value))
+
+
+def predict_values(forest, X: np.ndarray, threads: int = 1):
+    """Forests with leaf values: out = bias + scale * sum over trees of the
+    value of the leaf reached (every term exact in fp64, summed in fp64).
+
+    Returns dict(leaf [n][T], sum [n] fp64, abs [n] fp64 = sum of |value|,
+    out [n] fp64, visits int)."""
+    if forest.leaf_value is None:
+        raise ValueError("the forest has no leaf values")
+    r = predict(forest, X, leaves=True, votes=False, classes=False, threads=threads)
+    leaf = r["leaf"]
+    vals = forest.leaf_value[forest.node_begin[:-1][None, :] + leaf].astype(np.float64)
+    s = vals.sum(axis=1)
+    return dict(leaf=leaf, sum=s, abs=np.abs(vals).sum(axis=1),
+                out=forest.value_bias + forest.value_scale * s, visits=r["visits"])
+
+
+def value_tolerance(forest, abs_sum: np.ndarray) -> np.ndarray:
+    """Per-row bound on |float32 result - exact result| for a float32
+    evaluation that adds the T leaf values in any order and then computes
+    bias + scale * sum: recursive summation in any order is within
+    (T-1) u / (1 - (T-1) u) * sum|v| of the exact sum (u = 2^-24, Higham,
+    Accuracy and Stability of Numerical Algorithms, Sec. 4.2), and the
+    final multiply-add adds at most two roundings; (T + 2) u covers both
+    with a margin."""
+    u = 2.0 ** -24
+    T = forest.n_trees
+    return (T + 2) * u * (abs(forest.value_bias) + abs(forest.value_scale) * abs_sum) * 1.01 + 1e-30
 
 
 class Layout:
