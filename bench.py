@@ -17,7 +17,11 @@ Workloads (--workload):
   ablation the layout ablation on the HBM-resident forest (the GPU counterpart
            of the paper's Figs. 4 and 6): plain BF, DF order, Stat, Stat from
            statistics counted on observations, Bin with levels 0..d, Bin with
-           the most visited nodes, and the autotuned layout.
+           the most visited nodes, and the autotuned layout;
+  regress  a regression forest with real leaf values (128 trees), 4,000,000
+           rows; output = mean of the trees' leaf values (fp_predict_values);
+  boosted  256 gradient-boosted trees of depth <= 6, 4,000,000 rows; output =
+           initial score + sum of leaf values.
 
 Prints one JSON line (rank 0).  Besides the headline value it reports the
 plain breadth-first GPU baseline on the same inputs (the faster of its two
@@ -57,12 +61,24 @@ WORKLOADS = {
     "serving": dict(rows=0, desc="4 resident forests (tiny, image, hbm, 64-tree 50-class 100-feature), Poisson "
                                  "arrivals, rows/request LogNormal(ln 32, 1.5) clipped to [1, 4096]"),
     "ablation": dict(rows=4_000_000, desc="layout ablation on the HBM-resident forest (256 trees, 4,000,000 rows)"),
+    "regress": dict(rows=4_000_000, desc="regression forest with leaf values: 128 trees (min leaf 5) on the hbm "
+                                         "features with a real target, 200k training rows; output = mean of trees"),
+    "boosted": dict(rows=4_000_000, desc="gradient-boosted shallow trees: 256 rounds of depth <= 6, learning rate "
+                                         "0.1, 30k training rows; output = initial score + sum of trees"),
 }
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
 HBM_LAYOUTS = [(4, 9, 1), (3, 9, 1), (2, 9, 1), (3, 8, 1), (1, 10, 1), (16, 5, 1), (3, 8, 0)]  # (B, d, head_select)
 HBM_LAUNCHES = [(768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3), (1024, 32, 16, 3)]  # tile, warps, refill, buffers
+# the value workloads: the regression forest's trees resemble the hbm ones; the
+# boosted trees (depth <= 6) fit whole in a level head of depth 5
+TUNE = {
+    "hbm": (HBM_LAYOUTS, HBM_LAUNCHES),
+    "regress": ([(4, 9, 1), (2, 9, 1), (3, 8, 1), (16, 5, 1)], HBM_LAUNCHES),
+    "boosted": ([(16, 5, 1), (32, 5, 1), (8, 5, 1), (64, 5, 1)],
+                [(768, 32, 16, 3), (1024, 32, 16, 3), (512, 16, 16, 3), (1024, 32, 32, 2)]),
+}
 
 
 def parse():
@@ -173,13 +189,17 @@ def cpu_sample(forest, X, target_s: float, threads: int):
     """Oracle on a bounded prefix of the workload's rows: returns obs/s,
     visits per observation, the sample size and the seconds taken."""
     import oracle
+    if getattr(forest, "leaf_value", None) is not None:
+        call = lambda Xs: oracle.predict_values(forest, Xs, threads=threads)  # noqa: E731
+    else:
+        call = lambda Xs: oracle.predict(forest, Xs, leaves=False, votes=False, threads=threads)  # noqa: E731
     n = min(2000, X.shape[0])
     t0 = time.perf_counter()
-    oracle.predict(forest, X[:n], leaves=False, votes=False, threads=threads)
+    call(X[:n])
     dt = max(time.perf_counter() - t0, 1e-6)
     m = int(min(X.shape[0], max(n, n * target_s / dt)))
     t0 = time.perf_counter()
-    r = oracle.predict(forest, X[:m], leaves=False, votes=False, threads=threads)
+    r = call(X[:m])
     dt = time.perf_counter() - t0
     return m / dt, r["visits"] / m, m, dt
 
@@ -213,23 +233,30 @@ def run_reference(args, ws, rank):
         return
     import datagen
     import oracle
-    name = args.workload if args.workload in ("hbm", "image", "tiny") else "hbm"
+    name = args.workload if args.workload in ("hbm", "image", "tiny", "regress", "boosted") else "hbm"
     forest = datagen.forest(name)
     n_full = args.rows or WORKLOADS[name]["rows"]
     threads = oracle.default_threads()
+
+    def call(Xs):
+        if forest.leaf_value is not None:
+            oracle.predict_values(forest, Xs, threads=threads)
+        else:
+            oracle.predict(forest, Xs, leaves=False, votes=False, threads=threads)
+
     probe_rows = min(2000, n_full)
     X, _ = datagen.test_rows(name, probe_rows)
     t0 = time.perf_counter()
-    oracle.predict(forest, X, leaves=False, votes=False, threads=threads)
+    call(X)
     dt = max(time.perf_counter() - t0, 1e-6)
     m = int(min(n_full, max(probe_rows, probe_rows * 2.0 / dt)))  # ~2 s of CPU work per step
     X, _ = datagen.test_rows(name, m)
     for _ in range(args.warmup):
-        oracle.predict(forest, X, leaves=False, votes=False, threads=threads)
+        call(X)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.predict(forest, X, leaves=False, votes=False, threads=threads)
+        call(X)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = m * args.steps / total
@@ -258,8 +285,7 @@ def tuned_forest(args, forest, X, name):
                      bin_buffers=args.bin_buffers)
     else:
         sample = X[: min(X.shape[0], 1 << 20)]
-        layouts = HBM_LAYOUTS if name == "hbm" else None
-        launches = HBM_LAUNCHES if name == "hbm" else None
+        layouts, launches = TUNE.get(name, (None, None))
         best = at.autotune(forest, sample, layouts=layouts, launches=launches)
         tuning = {k: best[k] for k in at.LAYOUT_KEYS + at.LAUNCH_KEYS}
         tuning["candidates"] = len([r for r in best["table"] if "ms" in r])
@@ -284,9 +310,16 @@ def run_packed(args, ws, rank, local):
     df, tuning = tuned_forest(args, forest, X, name)
     info = df.info
     stream = torch.cuda.Stream(device=dev)
-    votes = torch.empty((n, C), dtype=torch.int32, device=dev)
-    cls = torch.empty((n,), dtype=torch.int32, device=dev)
+    values = forest.leaf_value is not None  # regression / boosted: a float per row instead of votes and classes
+    votes = None if values else torch.empty((n, C), dtype=torch.int32, device=dev)
+    cls = torch.empty((n,), dtype=torch.float32 if values else torch.int32, device=dev)
     torch.cuda.synchronize()
+
+    def step(Xs, out_votes, out, s):
+        if values:
+            fp.fp_predict_values(df, Xs, out, forest.value_scale, forest.value_bias, stream=s)
+        else:
+            fp.fp_predict(df, Xs, out_votes, out, stream=s)
 
     def barrier():
         if ws > 1:
@@ -294,7 +327,7 @@ def run_packed(args, ws, rank, local):
             dist.barrier()
 
     for _ in range(args.warmup):
-        fp.fp_predict(df, X, votes, cls, stream=stream)
+        step(X, votes, cls, stream)
     torch.cuda.synchronize()
     status = df.sync_status(stream)
     if status != fp.FP_OK:
@@ -310,7 +343,7 @@ def run_packed(args, ws, rank, local):
     start.record(stream)
     for i in range(args.steps):
         ev[i][0].record(stream)
-        fp.fp_predict(df, X, votes, cls, stream=stream)
+        step(X, votes, cls, stream)
         ev[i][1].record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
@@ -329,22 +362,32 @@ def run_packed(args, ws, rank, local):
     plain = None
     if not args.no_plain:
         pf = fp.fp_plain_build(forest)
-        pv = torch.empty((n, C), dtype=torch.int32, device=dev)
-        pc = torch.empty((n,), dtype=torch.int32, device=dev)
+        pv = None if values else torch.empty((n, C), dtype=torch.int32, device=dev)
+        pc = torch.empty((n,), dtype=cls.dtype, device=dev)
+
+        def plain_step(order):
+            if values:
+                fp.fp_plain_predict_values(pf, X, order, pc, forest.value_scale, forest.value_bias, stream=stream)
+            else:
+                fp.fp_plain_predict(pf, X, order, pv, pc, stream=stream)
+
         best = None
         for order, oname in ((fp.FP_PLAIN_OBS_FASTEST, "obs_fastest"), (fp.FP_PLAIN_TREE_FASTEST, "tree_fastest")):
-            fp.fp_plain_predict(pf, X, order, pv, pc, stream=stream)
+            plain_step(order)
             torch.cuda.synchronize()
             ks = max(2, args.steps // 4)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(ks):
-                fp.fp_plain_predict(pf, X, order, pv, pc, stream=stream)
+                plain_step(order)
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / ks
-            cand = {"order": oname, "value": n / (ms / 1e3), "ms_per_step": ms,
-                    "same_classes": bool(torch.equal(pc, cls))}
+            cand = {"order": oname, "value": n / (ms / 1e3), "ms_per_step": ms}
+            if values:
+                cand["max_abs_diff"] = float((pc - cls).abs().max())
+            else:
+                cand["same_classes"] = bool(torch.equal(pc, cls))
             if best is None or cand["value"] > best["value"]:
                 best = cand
         plain = dict(best, unit="observations/s", layout_bytes=pf.nbytes())
@@ -353,7 +396,7 @@ def run_packed(args, ws, rank, local):
 
     # end to end through host buffers: pinned rows in, classes out, every step
     Xpin = torch.from_numpy(Xh).pin_memory()
-    cls_host = torch.empty((n,), dtype=torch.int32).pin_memory()
+    cls_host = torch.empty((n,), dtype=cls.dtype).pin_memory()
     Xd2 = torch.empty_like(X)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
@@ -362,7 +405,7 @@ def run_packed(args, ws, rank, local):
         a.record(stream)
         for _ in range(e2e_steps):
             Xd2.copy_(Xpin, non_blocking=True)
-            fp.fp_predict(df, Xd2, None, cls, stream=stream)
+            step(Xd2, None, cls, stream)
             cls_host.copy_(cls, non_blocking=True)
         b.record(stream)
     torch.cuda.synchronize()
@@ -376,13 +419,38 @@ def run_packed(args, ws, rank, local):
     import oracle
     threads = oracle.default_threads()
     cpu_value, visits_per_obs, m, cpu_s = cpu_sample(forest, Xh, args.cpu_seconds, threads)
-    bytes_per_obs = 8.0 * visits_per_obs + 4.0 * F + 4.0 * C + 4.0
+    # node records, the row, and the outputs (votes and class; or the leaf
+    # value read per tree and one float out)
+    bytes_per_obs = 8.0 * visits_per_obs + 4.0 * F + (4.0 * T + 4.0 if values else 4.0 * C + 4.0)
     avg_launch_ms = statistics.mean(per_launch_ms)
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "obs_tile", "warps_per_cta",
                                    "refill_lanes", "bin_buffers")}
     traffic = profiled_traffic(name, params, n)
+    kernel = "fp_traverse_kernel<values>" if values else "fp_traverse_kernel<votes>"
+    visits_per_s = visits_per_obs * n / (avg_launch_ms / 1e3)
+    if info["n_super"] == 0:
+        # every internal node sits in the bins' interleaved heads: the node
+        # reads come from shared memory, so the bound is the SMs' shared-memory
+        # load bandwidth (128 bytes per clock per SM), not HBM
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        smem_peak = sms * 128 * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e9
+        smem_achieved = 8.0 * visits_per_s / 1e9
+        roofline = {"bound": "alu", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+                    "frac": smem_achieved / smem_peak, "traffic": traffic,
+                    "peak_kind": f"derived: shared-memory loads, {sms} SMs x 128 B/clock x max SM clock",
+                    "kernel": kernel, "avg_launch_ms": avg_launch_ms, "bytes_per_obs": 8.0 * visits_per_obs,
+                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s,
+                    "hbm": {"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                            "note": "algorithmic bytes incl. node records served from shared memory"}}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+                    "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
+                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s,
+                    "l2": {"peak": l2_gbs, "achieved": achieved, "frac": achieved / l2_gbs, "unit": "GB/s",
+                           "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"}}
     out = base_line(args, ws, value, total_ms,
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
                      "n_classes": C, **params, "passes": info["passes"], "forest_bytes": info["total_bytes"],
@@ -394,12 +462,7 @@ def run_packed(args, ws, rank, local):
         "packed_vs_plain": (value / ws / plain["value"]) if plain else None,
         "e2e": e2e,
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "fp_traverse_kernel<false>",
-                     "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
-                     "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_obs * n / (avg_launch_ms / 1e3),
-                     "l2": {"peak": l2_gbs, "achieved": achieved, "frac": achieved / l2_gbs, "unit": "GB/s",
-                            "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"}},
+        "roofline": roofline,
         "cpu_baseline": {"value": cpu_value, "unit": "observations/s", "cores": threads, "kind": "oracle",
                          "sample": f"first {m} of {n} rows ({cpu_s:.1f} s)"},
         "clocks": clk,

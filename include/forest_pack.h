@@ -72,6 +72,11 @@ typedef struct fp_forest_desc {
     const int64_t *cardinality;     /* training count reaching the node; used to
                                        order children (Section III-A, Stat).
                                        NULL: children keep left-first order. */
+    const float *leaf_value;        /* NULL for a classification forest; else a
+                                       forest with real leaf values (regression
+                                       or boosted trees): the value of each leaf
+                                       (finite; entries of internal nodes are
+                                       ignored), evaluated by fp_predict_values */
 } fp_forest_desc;
 
 /* Layout and launch parameters; 0 selects the default (for interleave_depth,
@@ -199,6 +204,24 @@ int fp_predict(const fp_device_forest *forest, const float *X, int64_t n, uint32
 int fp_predict_noalloc(const fp_device_forest *forest, const float *X, int64_t n, uint32_t *out_votes,
                        int32_t *out_class, void *stream);
 
+/* Forests with real leaf values (packed from a descriptor with leaf_value;
+ * regression and boosted trees, the forest variants the paper names beside
+ * classification): the same traversal as fp_predict, then
+ *   out[i] = bias + scale * (sum over trees of the value of the leaf x_i reaches)
+ * computed in float32: the leaf values of a tile are added in shared memory
+ * with atomics, and across passes in global memory, in no fixed order, so
+ * the result is within (T + 2) * 2^-24 * (|bias| + |scale| * sum |value|) of
+ * the exact one (recursive summation in any order, then one multiply-add).
+ * Use scale = 1/T for a regression forest's mean, scale = 1 and bias = the
+ * initial score for a boosted ensemble.
+ *   X     device, [n][n_features] FP32 row-major
+ *   out   device, [n] float
+ * Errors: FP_EINVAL (also for a forest without leaf values), FP_ENOMEM,
+ * FP_ECUDA.  fp_predict, fp_predict_noalloc and fp_predict_batched refuse
+ * forests with leaf values (FP_EINVAL); fp_predict_leaves accepts them. */
+int fp_predict_values(const fp_device_forest *forest, const float *X, int64_t n, float scale, float bias,
+                      float *out, void *stream);
+
 /* Parity mode: the leaf each observation reaches in each tree.
  *   out_leaf   device, [n][n_trees] int32, tree-local node id of the leaf in
  *              the fp_forest_desc the forest was packed from
@@ -297,6 +320,14 @@ int fp_plain_build(const fp_forest_desc *desc, void *stream, fp_plain_forest **o
  * out_class (device [n] int32) may be NULL.  order: FP_PLAIN_*. */
 int fp_plain_predict(const fp_plain_forest *pf, const float *X, int64_t n, int32_t order, uint32_t *out_votes,
                      int32_t *out_class, void *stream);
+
+/* The plain layout of a forest with leaf values (the value sits in the leaf's
+ * record): out[i] = bias + scale * sum of the reached leaves' values, added
+ * with global float atomics in no fixed order (error bound as
+ * fp_predict_values).  out: device [n] float, zeroed on the stream here.
+ * Errors: FP_EINVAL (also for a forest without leaf values), FP_ECUDA. */
+int fp_plain_predict_values(const fp_plain_forest *pf, const float *X, int64_t n, int32_t order, float scale,
+                            float bias, float *out, void *stream);
 
 /* Bytes of the plain layout on the device. */
 int64_t fp_plain_bytes(const fp_plain_forest *pf);

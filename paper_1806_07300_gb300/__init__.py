@@ -38,7 +38,7 @@ class fp_forest_desc(ctypes.Structure):
     _fields_ = [("n_trees", ctypes.c_int32), ("n_features", ctypes.c_int32), ("n_classes", ctypes.c_int32),
                 ("tree_node_begin", ctypes.c_void_p), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
                 ("feature", ctypes.c_void_p), ("threshold", ctypes.c_void_p), ("leaf_class", ctypes.c_void_p),
-                ("cardinality", ctypes.c_void_p)]
+                ("cardinality", ctypes.c_void_p), ("leaf_value", ctypes.c_void_p)]
 
 
 class fp_pack_params(ctypes.Structure):
@@ -70,7 +70,8 @@ class fp_batch(ctypes.Structure):
 EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload", "fp_predict",
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
-           "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves", "fp_inject_fault"]
+           "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves", "fp_inject_fault", "fp_predict_values",
+           "fp_plain_predict_values"]
 
 _lib = None
 _lock = threading.Lock()
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
                 "fp_l2_read_probe": ([P, i64, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
                 "fp_count_leaves": ([P, i64, i32, P, P, P, P], ctypes.c_int),
                 "fp_inject_fault": ([P, i32, i64], ctypes.c_int),
+                "fp_predict_values": ([P, P, i64, ctypes.c_float, ctypes.c_float, P, P], ctypes.c_int),
+                "fp_plain_predict_values": ([P, P, i64, i32, ctypes.c_float, ctypes.c_float, P, P], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -153,6 +156,11 @@ def make_desc(forest, keep: list) -> fp_forest_desc:
     d.n_classes = int(forest.n_classes)
     (d.tree_node_begin, d.left, d.right, d.feature, d.threshold, d.leaf_class) = [a.ctypes.data for a in arrs[:6]]
     d.cardinality = arrs[6].ctypes.data if arrs[6] is not None else None
+    lv = getattr(forest, "leaf_value", None)
+    if lv is not None:
+        lv = _np(lv, np.float32)
+        keep.append(lv)
+        d.leaf_value = lv.ctypes.data
     return d
 
 
@@ -198,7 +206,11 @@ def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_ti
 def fp_upload(packed: "PackedForest", stream=None) -> "DeviceForest":
     out = ctypes.c_void_p()
     _check(lib().fp_upload(packed.handle, _stream_ptr(stream), ctypes.byref(out)), "fp_upload")
-    return DeviceForest(out.value, packed.info())
+    df = DeviceForest(out.value, packed.info())
+    src = packed.forest
+    if src is not None and getattr(src, "leaf_value", None) is not None:
+        df.value_scale, df.value_bias = src.value_scale, src.value_bias
+    return df
 
 
 def fp_predict(forest: "DeviceForest", X, out_votes=None, out_class=None, stream=None) -> None:
@@ -208,6 +220,14 @@ def fp_predict(forest: "DeviceForest", X, out_votes=None, out_class=None, stream
     vp = _dptr(out_votes, _torch().int32, (n, info["n_classes"]), "out_votes") if out_votes is not None else None
     cp = _dptr(out_class, _torch().int32, (n,), "out_class") if out_class is not None else None
     _check(lib().fp_predict(forest.handle, xp, n, vp, cp, _stream_ptr(stream)), "fp_predict")
+
+
+def fp_predict_values(forest: "DeviceForest", X, out, scale: float, bias: float, stream=None) -> None:
+    """Forests with leaf values: out[i] = bias + scale * sum of leaf values."""
+    n = X.shape[0]
+    xp = _dptr(X, _torch().float32, (n, forest.info["n_features"]), "X")
+    op = _dptr(out, _torch().float32, (n,), "out")
+    _check(lib().fp_predict_values(forest.handle, xp, n, scale, bias, op, _stream_ptr(stream)), "fp_predict_values")
 
 
 def fp_predict_noalloc(forest: "DeviceForest", X, out_votes=None, out_class=None, stream=None) -> None:
@@ -307,6 +327,9 @@ class PackedForest:
 class DeviceForest:
     """A packed forest resident on the current device (fp_upload)."""
 
+    value_scale = None  # forests with leaf values: the scale and bias of their output
+    value_bias = None
+
     def __init__(self, handle: int, info: dict):
         self.handle = handle
         i = fp_packed_info()
@@ -329,6 +352,15 @@ class DeviceForest:
         c = T.empty((n,), dtype=T.int32, device=X.device) if classes else None
         fp_predict(self, X, v, c, stream)
         return v, c
+
+    def predict_values(self, X, scale: float | None = None, bias: float | None = None, stream=None):
+        """bias + scale * the sum of leaf values per row (a float32 tensor);
+        scale and bias default to those of the forest that was packed."""
+        T = _torch()
+        out = T.empty((X.shape[0],), dtype=T.float32, device=X.device)
+        fp_predict_values(self, X, out, self.value_scale if scale is None else scale,
+                          self.value_bias if bias is None else bias, stream)
+        return out
 
     def predict_leaves(self, X, stream=None):
         T = _torch()
@@ -361,6 +393,8 @@ class PlainForest:
         _check(lib().fp_plain_build(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(out)), "fp_plain_build")
         self.handle = out.value
         self.n_trees, self.n_features, self.n_classes = forest.n_trees, forest.n_features, forest.n_classes
+        self.value_scale = getattr(forest, "value_scale", 1.0)
+        self.value_bias = getattr(forest, "value_bias", 0.0)
 
     def nbytes(self) -> int:
         return lib().fp_plain_bytes(self.handle)
@@ -374,6 +408,13 @@ class PlainForest:
             out_class = T.empty((n,), dtype=T.int32, device=X.device)
         fp_plain_predict(self, X, order, out_votes, out_class, stream)
         return out_votes, out_class
+
+    def predict_values(self, X, order: int = FP_PLAIN_OBS_FASTEST, out=None, stream=None):
+        T = _torch()
+        if out is None:
+            out = T.empty((X.shape[0],), dtype=T.float32, device=X.device)
+        fp_plain_predict_values(self, X, order, out, self.value_scale, self.value_bias, stream)
+        return out
 
     def release(self) -> None:
         if self.handle:
@@ -452,6 +493,15 @@ def _postorder(left, right):
 
 def fp_plain_build(forest, stream=None) -> PlainForest:
     return PlainForest(forest, stream)
+
+
+def fp_plain_predict_values(pf: PlainForest, X, order, out, scale: float, bias: float, stream=None) -> None:
+    T = _torch()
+    n = X.shape[0]
+    xp = _dptr(X, T.float32, (n, pf.n_features), "X")
+    op = _dptr(out, T.float32, (n,), "out")
+    _check(lib().fp_plain_predict_values(pf.handle, xp, n, order, scale, bias, op, _stream_ptr(stream)),
+           "fp_plain_predict_values")
 
 
 def fp_plain_predict(pf: PlainForest, X, order, out_votes, out_class=None, stream=None) -> None:

@@ -17,7 +17,7 @@ import time
 
 import numpy as np
 
-from . import FPError, fp_pack_forest, fp_predict, fp_upload
+from . import FPError, fp_pack_forest, fp_predict, fp_predict_values, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
 LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select")
@@ -79,17 +79,32 @@ def _cache_path() -> str:
     return os.path.join(root, "autotune.json")
 
 
-def _time_predict(df, X, votes, cls, reps: int) -> float:
+def _time_predict(df, X, out, reps: int) -> float:
+    """Milliseconds per call: classes (int32 out) or, for a forest with leaf
+    values, the value output (float32 out)."""
     import torch
-    fp_predict(df, X, None, cls)
+    if out.dtype == torch.float32:
+        call = lambda: fp_predict_values(df, X, out, df.value_scale, df.value_bias)  # noqa: E731
+    else:
+        call = lambda: fp_predict(df, X, None, out)  # noqa: E731
+    call()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(reps):
-        fp_predict(df, X, None, cls)
+        call()
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def _same(ref, out) -> bool:
+    """Classes must agree exactly; value outputs (float sums in no fixed
+    order) to within a relative 1e-4."""
+    import torch
+    if out.dtype != torch.float32:
+        return bool(torch.equal(ref, out))
+    return bool(torch.all((ref - out).abs() <= 1e-4 * (1.0 + ref.abs())))
 
 
 def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: bool = True,
@@ -110,7 +125,8 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
         if key in cache:
             return cache[key]
     layouts = layouts or candidate_layouts(forest.n_trees)
-    cls = torch.empty((X.shape[0],), dtype=torch.int32, device=X.device)
+    values = getattr(forest, "leaf_value", None) is not None
+    cls = torch.empty((X.shape[0],), dtype=torch.float32 if values else torch.int32, device=X.device)
     table = []
     ref = None
     for lay in layouts:
@@ -132,10 +148,10 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
                 table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=tile,
                                   warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf, error=str(e)))
                 continue
-            ms = _time_predict(df, X, None, cls, reps)
+            ms = _time_predict(df, X, cls, reps)
             if ref is None:
                 ref = cls.clone()
-            same = bool(torch.equal(ref, cls))
+            same = _same(ref, cls)
             row = dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=df.info["obs_tile"],
                        warps_per_cta=warps, bin_buffers=nbuf,
                        refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)

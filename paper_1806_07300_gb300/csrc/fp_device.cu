@@ -32,8 +32,8 @@ struct fp_device_forest {
     int32_t refill = 8;
     int32_t head_smem = 0;
     int32_t nbuf = 3;                          // bin-block buffers
-    size_t smem_votes = 0, smem_leaves = 0;
-    int32_t grid_votes = 0, grid_leaves = 0;  // resident CTAs for a persistent launch
+    size_t smem_votes = 0, smem_leaves = 0, smem_values = 0;
+    int32_t grid_votes = 0, grid_leaves = 0, grid_values = 0;  // resident CTAs for a persistent launch
     int32_t spin_limit = FP_SPIN_LIMIT;       // fault injection may lower it
     int32_t stall = 0;                        // fault injection: bin waits run out
 };
@@ -91,14 +91,14 @@ size_t smem_bytes(int R, int F, int head_smem, int nbuf, int C, int warps, bool 
 
 // The kernel variant for a block size: up to 512 threads run the three-CTAs-
 // per-SM build (<= 42 registers), larger blocks the one-CTA build.
-template <bool LEAVES>
+template <int MODE>
 void (*traverse_kernel(int threads))(TravParams) {
-    return threads <= 512 ? fp_traverse_kernel<LEAVES, 3> : fp_traverse_kernel<LEAVES, 1>;
+    return threads <= 512 ? fp_traverse_kernel<MODE, 3> : fp_traverse_kernel<MODE, 1>;
 }
 
-template <bool LEAVES>
+template <int MODE>
 int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
-    auto kern = traverse_kernel<LEAVES>(f->threads);
+    auto kern = traverse_kernel<MODE>(f->threads);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
@@ -142,10 +142,15 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     g.nbuf = nbuf;
     g.smem_votes = smem_bytes(R, F, f->head_smem, nbuf, C, warps, false);
     g.smem_leaves = smem_bytes(R, F, f->head_smem, nbuf, C, warps, true);
-    int rc = configure<false>(&g, g.smem_votes, &g.grid_votes);
+    int rc = configure<FP_MODE_VOTES>(&g, g.smem_votes, &g.grid_votes);
     if (rc) return rc;
-    rc = configure<true>(&g, g.smem_leaves, &g.grid_leaves);
+    rc = configure<FP_MODE_LEAVES>(&g, g.smem_leaves, &g.grid_leaves);
     if (rc) return rc;
+    if (f->hdr.n_values > 0) {  // one float per row instead of the class votes
+        g.smem_values = smem_bytes(R, F, f->head_smem, nbuf, 1, warps, false);
+        rc = configure<FP_MODE_VALUES>(&g, g.smem_values, &g.grid_values);
+        if (rc) return rc;
+    }
     // the batched kernel may host any resident forest: allow it all of shared memory
     cudaError_t e2 = cudaFuncSetAttribute(fp_traverse_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)budget);
@@ -158,6 +163,8 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     f->smem_leaves = g.smem_leaves;
     f->grid_votes = g.grid_votes;
     f->grid_leaves = g.grid_leaves;
+    f->smem_values = g.smem_values;
+    f->grid_values = g.grid_values;
     return FP_OK;
 }
 
@@ -181,6 +188,8 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.head_smem = f->head_smem;
     p.nbuf = f->nbuf;
     p.levels = h.head_select == 1;
+    p.leaf_val = reinterpret_cast<const float *>(f->d_image + h.off_values);
+    p.n_vals = (uint32_t)h.n_values;
     p.depth = h.depth;
     p.refill = f->refill;
     p.status = f->d_status;
@@ -273,6 +282,10 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
         fp_set_error("fp_predict: bad arguments");
         return FP_EINVAL;
     }
+    if (f->hdr.n_values > 0) {
+        fp_set_error("fp_predict: the forest has leaf values; use fp_predict_values");
+        return FP_EINVAL;
+    }
     if (n == 0 || (!out_votes && !out_class)) return FP_OK;
     int rc = check_device(f);
     if (rc) return rc;
@@ -307,10 +320,52 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    traverse_kernel<false>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<FP_MODE_VOTES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (scratch) cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
+    return FP_OK;
+}
+
+extern "C" int fp_predict_values(const fp_device_forest *f, const float *X, int64_t n, float scale, float bias,
+                                 float *out, void *stream) {
+    if (!f || n < 0 || (n > 0 && (!X || !out))) {
+        fp_set_error("fp_predict_values: bad arguments");
+        return FP_EINVAL;
+    }
+    if (f->hdr.n_values <= 0) {
+        fp_set_error("fp_predict_values: the forest was packed without leaf values");
+        return FP_EINVAL;
+    }
+    if (n == 0) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const FpImageHeader &h = f->hdr;
+    TravParams p = base_params(f, X, n);
+    p.n_passes = h.n_passes;
+    p.n_items = p.n_tiles * h.n_passes;
+    p.vscale = scale;
+    p.vbias = bias;
+    p.out_val = out;
+    void *scratch = nullptr;
+    cudaError_t e;
+    if (h.n_passes > 1) {  // a float accumulator per row and a counter per tile
+        const size_t acc_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
+        const size_t bytes = acc_bytes + (size_t)p.n_tiles * 4;
+        rc = scratch_alloc(f->device, &scratch, bytes, s);
+        if (rc) return rc;
+        e = cudaMemsetAsync(scratch, 0, bytes, s);
+        if (e != cudaSuccess) { cudaFreeAsync(scratch, s); return cuda_fail(e, "cudaMemsetAsync(scratch)"); }
+        uint8_t *sc = static_cast<uint8_t *>(scratch);
+        p.acc_val = reinterpret_cast<float *>(sc);
+        p.tile_done = reinterpret_cast<uint32_t *>(sc + acc_bytes);
+    }
+    const int64_t grid = std::min<int64_t>(p.n_items, f->grid_values);
+    traverse_kernel<FP_MODE_VALUES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_values, s>>>(p);
+    e = cudaGetLastError();
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<values> launch");
     return FP_OK;
 }
 
@@ -350,6 +405,10 @@ extern "C" int fp_predict_noalloc(const fp_device_forest *f, const float *X, int
         fp_set_error("fp_predict_noalloc: bad arguments");
         return FP_EINVAL;
     }
+    if (f->hdr.n_values > 0) {
+        fp_set_error("fp_predict_noalloc: the forest has leaf values; use fp_predict_values");
+        return FP_EINVAL;
+    }
     if (n == 0 || (!out_votes && !out_class)) return FP_OK;
     int rc = check_device(f);
     if (rc) return rc;
@@ -387,7 +446,7 @@ extern "C" int fp_predict_noalloc(const fp_device_forest *f, const float *X, int
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    traverse_kernel<false>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<FP_MODE_VOTES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
     return FP_OK;
@@ -408,7 +467,7 @@ extern "C" int fp_predict_leaves(const fp_device_forest *f, const float *X, int6
     p.n_items = p.n_tiles * f->hdr.n_passes;
     p.out_leaf = out_leaf;
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_leaves);
-    traverse_kernel<true>(f->threads)<<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
+    traverse_kernel<FP_MODE_LEAVES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<leaves> launch");
     return FP_OK;
@@ -574,6 +633,10 @@ extern "C" int fp_predict_batched(const fp_device_forest *const *forests, const 
     for (int32_t i = 0; i < k; ++i) {
         if (!forests[i] || batches[i].n < 0 || (batches[i].n > 0 && !batches[i].X)) {
             fp_set_error("fp_predict_batched: bad batch %d", i);
+            return FP_EINVAL;
+        }
+        if (forests[i]->hdr.n_values > 0) {
+            fp_set_error("fp_predict_batched: forest %d has leaf values; use fp_predict_values", i);
             return FP_EINVAL;
         }
         int rc = check_device(forests[i]);

@@ -44,8 +44,13 @@
 // an exit holding that leaf.  nranks + nexits <= 2048 (so d <= 9).
 //
 // A reference (exit entry or super-node exit) is a uint32:
-//   bit 31 = 1: a leaf, bits 30..0 = its class
+//   bit 31 = 1: a leaf, bits 30..0 = its class (classification forests) or
+//               its slot in values[] (forests with leaf values)
 //   bit 31 = 0: a super-node, the index into deep[] (so fewer than 2^31)
+//
+// Forests with leaf values also hold values[n_values] (float, one slot per
+// leaf, numbered tree by tree in node order) at off_values, inside the
+// classification part of the image.
 //
 // Super-node (32 bytes, one L2 sector, 32-byte aligned): a node v below the
 // head together with its two children, i.e. two levels of the tree resolved
@@ -106,4 +111,5 @@ struct FpImageHeader {
     int64_t total_bytes;           // end of the image (incl. parity tables)
     int64_t head_bytes_total, pass_bytes;
     int64_t n_internal;            // internal nodes of the forest
+    int64_t n_values, off_values;  // leaf-value slots (0 for a classification forest)
 };

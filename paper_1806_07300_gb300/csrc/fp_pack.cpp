@@ -122,6 +122,8 @@ struct TreeLayout {
     std::vector<int32_t> exits;      // node id behind each exit (leaf or deep root)
     std::vector<int32_t> sn_root;    // root node of each super-node, in layout order
     std::vector<int32_t> sn_index;   // node id -> super-node index (-1 if it roots none)
+    std::vector<int32_t> leaf_rank;  // forests with leaf values: node id -> rank among the tree's leaves
+    int64_t value_base = -1;         // forests with leaf values: the tree's first value slot
 };
 
 // The four exits of the super-node rooted at v: the grandchildren through
@@ -275,10 +277,13 @@ int finish_super(const TreeRef &t, TreeLayout &out, int32_t ti) {
     return FP_OK;
 }
 
-// A leaf's class, or the global index of the super-node rooted at v (base =
-// the tree's first super-node).
+// A leaf's class (or, in a forest with leaf values, its value slot), or the
+// global index of the super-node rooted at v (base = the tree's first
+// super-node).
 uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base) {
-    return t.leaf(v) ? (FP_REF_LEAF | (uint32_t)t.Cl[v]) : (uint32_t)(base + lay.sn_index[v]);
+    if (!t.leaf(v)) return (uint32_t)(base + lay.sn_index[v]);
+    if (lay.value_base >= 0) return FP_REF_LEAF | (uint32_t)(lay.value_base + lay.leaf_rank[v]);
+    return FP_REF_LEAF | (uint32_t)t.Cl[v];
 }
 
 void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base, FpSuper &sn,
@@ -352,7 +357,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         std::vector<TreeLayout> lays((size_t)T);
         std::vector<uint8_t> seen;
         std::vector<int64_t> deep_count((size_t)T);
-        int64_t n_internal = 0;
+        int64_t n_internal = 0, n_values = 0;
         for (int32_t t = 0; t < T; ++t) {
             int64_t b = desc->tree_node_begin[t], e = desc->tree_node_begin[t + 1];
             if (e < b) {
@@ -367,6 +372,26 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             if (rc) return rc;
             deep_count[t] = (int64_t)lays[t].sn_root.size();
             for (int64_t v = 0; v < tr.m; ++v) n_internal += !tr.leaf((int32_t)v);
+            if (desc->leaf_value) {  // value slots: the tree's leaves in node order
+                TreeLayout &lay = lays[t];
+                lay.value_base = n_values;
+                lay.leaf_rank.assign((size_t)tr.m, -1);
+                int32_t k = 0;
+                for (int64_t v = 0; v < tr.m; ++v) {
+                    if (!tr.leaf((int32_t)v)) continue;
+                    const float val = desc->leaf_value[b + v];
+                    if (!(val - val == 0.0f)) {
+                        fp_set_error("fp_pack_forest: tree %d leaf %lld has a non-finite value", t, (long long)v);
+                        return FP_EINVAL;
+                    }
+                    lay.leaf_rank[v] = k++;
+                }
+                n_values += k;
+                if (n_values >= (int64_t)FP_REF_LEAF) {
+                    fp_set_error("fp_pack_forest: more than 2^31 leaves");
+                    return FP_EUNSUPPORTED;
+                }
+            }
         }
 
         // ---- section sizes
@@ -450,6 +475,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.off_tree_base = off; off = align_up(off + 4 * (int64_t)T, 256);
         h.off_heads = off; off = align_up(off + head_total, 256);
         h.off_deep = off; off = align_up(off + (int64_t)sizeof(FpSuper) * n_deep, 256);
+        h.n_values = n_values;
+        h.off_values = off; off = align_up(off + 4 * n_values, 256);
         h.class_bytes = off;
         h.off_pheads = off; off = align_up(off + phead_total, 256);
         h.off_deep_leaf = off; off = align_up(off + 16 * n_deep, 256);
@@ -526,6 +553,17 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                     exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v, tree_base[t]);
                     pexits[(int64_t)e * bn.stride + k] = tr.leaf(v) ? v : -1;
                 }
+            }
+        }
+
+        // ---- leaf values, one slot per leaf
+        if (n_values) {
+            float *vals = reinterpret_cast<float *>(img + h.off_values);
+            for (int32_t t = 0; t < T; ++t) {
+                const int64_t nb = desc->tree_node_begin[t];
+                const TreeLayout &lay = lays[t];
+                for (size_t v = 0; v < lay.leaf_rank.size(); ++v)
+                    if (lay.leaf_rank[v] >= 0) vals[lay.value_base + lay.leaf_rank[v]] = desc->leaf_value[nb + v];
             }
         }
 

@@ -4,7 +4,9 @@
 // atomic vote per thread, then a separate argmax kernel; one launch per batch.
 //
 // Record {float thr; uint32 meta}, 8 bytes, per tree in breadth-first order:
-//   meta bit 31 = 1: leaf, meta & 0x7FFFFFFF = class
+//   meta bit 31 = 1: leaf, meta & 0x7FFFFFFF = class; in a forest with leaf
+//                    values the first word holds the leaf's value instead
+//                    of a threshold
 //   meta bit 31 = 0: [30:21] feature, [20:0] tree-local index of the left
 //                    child; the right child follows it (siblings are adjacent
 //                    in breadth-first order).
@@ -21,6 +23,7 @@
 struct fp_plain_forest {
     int device = -1;
     int32_t T = 0, F = 0, C = 0;
+    bool values = false;  // leaf records carry values
     uint2 *d_recs = nullptr;
     int64_t *d_tree_off = nullptr;
     int64_t n_recs = 0;
@@ -60,6 +63,41 @@ __global__ void plain_vote_kernel(const uint2 *__restrict__ recs, const int64_t 
         const float v = __ldg(x + ((rec.y >> 21) & 1023u));
         node = (rec.y & 0x1FFFFFu) + (v <= __uint_as_float(rec.x) ? 0u : 1u);
     }
+}
+
+// Forests with leaf values: thread per (observation, tree), the leaf's value
+// added to the row with a global float atomic.
+__global__ void plain_value_kernel(const uint2 *__restrict__ recs, const int64_t *__restrict__ tree_off,
+                                   const float *__restrict__ X, int64_t n, int32_t T, int32_t F, int32_t order,
+                                   float *__restrict__ sum) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n * T) return;
+    int64_t i;
+    int32_t t;
+    if (order == FP_PLAIN_OBS_FASTEST) {
+        t = (int32_t)(tid / n);
+        i = tid - (int64_t)t * n;
+    } else {
+        i = tid / T;
+        t = (int32_t)(tid - i * T);
+    }
+    const uint2 *tree = recs + tree_off[t];
+    const float *x = X + i * F;
+    uint32_t node = 0;
+    for (;;) {
+        const uint2 rec = __ldg(tree + node);
+        if (rec.y & 0x80000000u) {
+            atomicAdd(sum + i, __uint_as_float(rec.x));
+            return;
+        }
+        const float v = __ldg(x + ((rec.y >> 21) & 1023u));
+        node = (rec.y & 0x1FFFFFu) + (v <= __uint_as_float(rec.x) ? 0u : 1u);
+    }
+}
+
+__global__ void plain_value_finish_kernel(float *__restrict__ out, int64_t n, float scale, float bias) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = bias + scale * out[i];
 }
 
 __global__ void plain_argmax_kernel(const uint32_t *__restrict__ votes, int64_t n, int32_t C,
@@ -124,6 +162,14 @@ extern "C" int fp_plain_build(const fp_forest_desc *desc, void *stream, fp_plain
                         return FP_EINVAL;
                     }
                     r.x = 0;
+                    if (desc->leaf_value) {
+                        const float val = desc->leaf_value[b + v];
+                        if (!(val - val == 0.0f)) {
+                            fp_set_error("fp_plain_build: tree %d leaf %d has a non-finite value", t, v);
+                            return FP_EINVAL;
+                        }
+                        memcpy(&r.x, &val, 4);
+                    }
                     r.y = 0x80000000u | (uint32_t)c;
                 } else {
                     const int32_t f = desc->feature[b + v];
@@ -147,6 +193,7 @@ extern "C" int fp_plain_build(const fp_forest_desc *desc, void *stream, fp_plain
     fp_plain_forest *pf = new (std::nothrow) fp_plain_forest;
     if (!pf) return FP_ENOMEM;
     pf->T = T; pf->F = F; pf->C = C; pf->n_recs = (int64_t)recs.size();
+    pf->values = desc->leaf_value != nullptr;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&pf->device);
     if (e == cudaSuccess) e = cudaMalloc(&pf->d_recs, recs.size() * sizeof(uint2));
@@ -174,6 +221,10 @@ extern "C" int fp_plain_predict(const fp_plain_forest *pf, const float *X, int64
         fp_set_error("fp_plain_predict: bad arguments");
         return FP_EINVAL;
     }
+    if (pf->values) {
+        fp_set_error("fp_plain_predict: the forest has leaf values; use fp_plain_predict_values");
+        return FP_EINVAL;
+    }
     if (n == 0) return FP_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(out_votes, 0, (size_t)n * pf->C * 4, s);
@@ -194,6 +245,37 @@ extern "C" int fp_plain_predict(const fp_plain_forest *pf, const float *X, int64
         e = cudaGetLastError();
         if (e != cudaSuccess) return plain_fail(e, "plain_argmax_kernel launch");
     }
+    return FP_OK;
+}
+
+extern "C" int fp_plain_predict_values(const fp_plain_forest *pf, const float *X, int64_t n, int32_t order,
+                                       float scale, float bias, float *out, void *stream) {
+    if (!pf || n < 0 || (n > 0 && (!X || !out)) ||
+        (order != FP_PLAIN_OBS_FASTEST && order != FP_PLAIN_TREE_FASTEST)) {
+        fp_set_error("fp_plain_predict_values: bad arguments");
+        return FP_EINVAL;
+    }
+    if (!pf->values) {
+        fp_set_error("fp_plain_predict_values: the forest was built without leaf values");
+        return FP_EINVAL;
+    }
+    if (n == 0) return FP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * 4, s);
+    if (e != cudaSuccess) return plain_fail(e, "cudaMemsetAsync(out)");
+    const int threads = 256;
+    const int64_t blocks = (n * pf->T + threads - 1) / threads;
+    if (blocks > INT32_MAX) {
+        fp_set_error("fp_plain_predict_values: batch too large for one launch");
+        return FP_EUNSUPPORTED;
+    }
+    plain_value_kernel<<<(unsigned)blocks, threads, 0, s>>>(pf->d_recs, pf->d_tree_off, X, n, pf->T, pf->F, order,
+                                                            out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return plain_fail(e, "plain_value_kernel launch");
+    plain_value_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, scale, bias);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return plain_fail(e, "plain_value_finish_kernel launch");
     return FP_OK;
 }
 

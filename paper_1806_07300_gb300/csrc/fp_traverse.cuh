@@ -36,7 +36,10 @@
 //      are added to a global accumulator and the CTA that finishes a tile's
 //      last pass (per-tile counter, no waiting) takes the argmax.
 // Parity mode writes the leaf id reached in every (observation, tree)
-// instead of voting.
+// instead of voting.  Values mode (forests with real leaf values: regression
+// and boosted trees) adds the leaf's value to a float per row instead, and
+// writes bias + scale * sum (several passes: summed in global memory, the
+// last pass's CTA writes it).
 //
 // Waits: cp.async.wait_group and __syncthreads are hardware waits; a wait for
 // a bin block polls its mbarrier at most spin_limit times (FP_SPIN_LIMIT
@@ -75,9 +78,19 @@ struct TravParams {
     uint32_t *acc;            // several passes: vote accumulator
     uint32_t *tile_done;      // several passes: per-tile pass counter
     int32_t *status;          // device status word
+    const float *leaf_val;    // forests with leaf values: value of each leaf slot
+    uint32_t n_vals;          // slots in leaf_val
+    float vscale, vbias;      // out = vbias + vscale * sum of leaf values
+    float *out_val;           // values mode: output per row
+    float *acc_val;           // values mode, several passes: per-row accumulator
     int32_t spin_limit;       // polls of a bin block's barrier before the wait gives up
     int32_t stall;            // fault injection: bin waits ignore completed copies (0 normally)
 };
+
+// What a kernel computes per (row, tree) task it finishes.
+#define FP_MODE_VOTES 0   // a vote for the leaf's class; then votes and the argmax class
+#define FP_MODE_LEAVES 1  // the leaf id (parity mode)
+#define FP_MODE_VALUES 2  // the leaf's value, summed per row; then bias + scale * sum
 
 #define FP_ERR_FLAG_DEVICE (-6)
 #define FP_ERR_FLAG_TIMEOUT (-5)
@@ -155,12 +168,18 @@ struct LaneTask {
     uint32_t ref;     // current super-node (index into deep)
 };
 
-// A finished task: vote, or record the leaf id in parity mode.
-template <bool LEAVES>
+// A finished task: vote, record the leaf id (parity mode) or add the leaf's
+// value to the row's sum (cls is then the leaf's value slot).
+template <int MODE>
 __device__ __forceinline__ void finish(const TravParams &p, uint32_t *svotes, int64_t row0, int r, int t,
                                        uint32_t cls, int32_t leaf_id) {
-    if (LEAVES) {
+    if (MODE == FP_MODE_LEAVES) {
         p.out_leaf[(row0 + r) * p.T + t] = leaf_id;
+    } else if (MODE == FP_MODE_VALUES) {
+        if (cls < p.n_vals)
+            atomicAdd(reinterpret_cast<float *>(svotes) + r, __ldg(p.leaf_val + cls));
+        else
+            report(p.status, FP_ERR_FLAG_DEVICE);
     } else if (cls < (uint32_t)p.C) {
         atomicAdd(&svotes[r * p.C + cls], 1u);
     } else {
@@ -192,7 +211,7 @@ __device__ __forceinline__ void deep_issue(const TravParams &p, const LaneTask &
     ld_super(p.deep + L.ref, w);
 }
 
-template <bool LEAVES>
+template <int MODE>
 __device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
                                             LaneTask &L, const uint32_t w[8]) {
     const int R = p.R;
@@ -206,8 +225,8 @@ __device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs
     if (nref & FP_REF_LEAF) {
         L.active = false;
         int32_t leaf_id = -1;
-        if (LEAVES) leaf_id = p.deep_leaf[4 * (int64_t)L.ref + 2 * d0 + d1];
-        finish<LEAVES>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
+        if (MODE == FP_MODE_LEAVES) leaf_id = p.deep_leaf[4 * (int64_t)L.ref + 2 * d0 + d1];
+        finish<MODE>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
     } else if (nref > L.ref) {  // super-nodes only point forward, so every walk ends
         L.ref = nref;
     } else {
@@ -258,15 +277,17 @@ __device__ __forceinline__ void cta_finish(CtaShared &sh) {
 // completes its barrier's phase k, so a wait needs the buffer's copy count
 // at the item's start (use0) plus bi / nbuf.  Counting per buffer keeps the
 // phases right when items of forests with different nbuf share a CTA.
-template <bool LEAVES>
+template <int MODE>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
+    constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
     const int R = p.R, F = p.F, C = p.C;
     float *xs = reinterpret_cast<float *>(smem);
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
     const int nbuf = p.nbuf;
     uint8_t *const hbuf0 = smem + xs_bytes;  // nbuf bin-block buffers, head_smem bytes each
     uint32_t *svotes = reinterpret_cast<uint32_t *>(smem + xs_bytes + nbuf * p.head_smem);
-    const int vote_bytes = LEAVES ? 0 : ((R * C * 4) + 15) & ~15;
+    const int CS = VALUES ? 1 : C;  // counters per row: class votes, or one float sum
+    const int vote_bytes = LEAVES ? 0 : ((R * CS * 4) + 15) & ~15;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     uint2 *ring = reinterpret_cast<uint2 *>(smem + xs_bytes + nbuf * p.head_smem + vote_bytes) + warp * FP_RING;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -347,7 +368,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
             for (int i = 0; i < nbuf && i < nbins; ++i) issue(ps.bin_begin + i, i);
     }
     if (!LEAVES)
-        for (int i = tid; i < rows * C; i += blockDim.x) svotes[i] = 0;
+        for (int i = tid; i < rows * CS; i += blockDim.x) svotes[i] = 0;
     cp_async_wait_all();
     __syncthreads();
 
@@ -443,7 +464,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 if (my && (er & FP_REF_LEAF)) {
                     int32_t leaf_id = -1;
                     if (LEAVES && e < (uint32_t)nexits) leaf_id = p.pheads[(bn.phead_off >> 2) + e * stride + k2];
-                    finish<LEAVES>(p, svotes, row0, r2, t2, er & 0x7FFFFFFFu, leaf_id);
+                    finish<MODE>(p, svotes, row0, r2, t2, er & 0x7FFFFFFFu, leaf_id);
                 }
                 const bool push = my && !(er & FP_REF_LEAF);
                 const unsigned pm = __ballot_sync(0xffffffffu, push);
@@ -453,7 +474,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 tail += __popc(pm);
                 __syncwarp();
             }
-            if (L.active) deep_finish<LEAVES>(p, xs, svotes, row0, L, w);
+            if (L.active) deep_finish<MODE>(p, xs, svotes, row0, L, w);
             pop_tasks(p, ring, head, tail, L, lt_mask);
         }
         // this warp reads the bin's block no more; the last warp refills the buffer
@@ -474,13 +495,36 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         if (L.active) {
             uint32_t w[8];
             deep_issue(p, L, w);
-            deep_finish<LEAVES>(p, xs, svotes, row0, L, w);
+            deep_finish<MODE>(p, xs, svotes, row0, L, w);
         }
     }
     __syncthreads();
 
+    // 5. values: bias + scale * the row's sum (several passes: summed in global
+    //    memory, the CTA finishing a tile's last pass writes the result)
+    if (VALUES && !*(volatile int *)&sh.abort) {
+        const float *sv = reinterpret_cast<const float *>(svotes);
+        if (p.n_passes == 1) {
+            for (int rr = tid; rr < rows; rr += blockDim.x) p.out_val[row0 + rr] = p.vbias + p.vscale * sv[rr];
+        } else {
+            float *dst = p.acc_val + row0;
+            for (int rr = tid; rr < rows; rr += blockDim.x) {
+                const float v = sv[rr];
+                if (v != 0.0f) atomicAdd(dst + rr, v);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) sh.last = atomicAdd(p.tile_done + tile, 1u) == (unsigned)(p.n_passes - 1);
+            __syncthreads();
+            if (sh.last) {
+                __threadfence();
+                for (int rr = tid; rr < rows; rr += blockDim.x)
+                    p.out_val[row0 + rr] = p.vbias + p.vscale * __ldcg(dst + rr);
+            }
+        }
+    }
     // 5. votes and class
-    if (!LEAVES && !*(volatile int *)&sh.abort) {
+    if (MODE == FP_MODE_VOTES && !*(volatile int *)&sh.abort) {
         if (p.n_passes == 1) {
             if (p.out_votes) {
                 uint32_t *dst = p.out_votes + row0 * C;
@@ -530,12 +574,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 // MINB = 1: one CTA of up to 1024 threads per SM (up to 64 registers a thread);
 // MINB = 3: up to three CTAs of up to 512 threads (at most 42 registers), for
 // launches whose shared memory leaves room for three CTAs.
-template <bool LEAVES, int MINB>
+template <int MODE, int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? 1024 : 512, MINB) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<LEAVES>(p, item, smem, sh);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE>(p, item, smem, sh);
     cta_finish(sh);
 }
 
@@ -564,7 +608,7 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         if (item >= total) break;
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
-        run_item<false>(bp.p[j], item - bp.item_begin[j], smem, sh);
+        run_item<FP_MODE_VOTES>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }

@@ -11,7 +11,8 @@ HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_trees", "<i4"), ("n_fe
                 ("warps_per_cta", "<i4"), ("max_head_bytes", "<i4"), ("refill_lanes", "<i4"), ("bin_buffers", "<i4"), ("n_super", "<i8"),
                 ("off_bins", "<i8"), ("off_passes", "<i8"), ("off_tree_base", "<i8"), ("off_heads", "<i8"),
                 ("off_deep", "<i8"), ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"),
-                ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8")],
+                ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8"),
+                ("n_values", "<i8"), ("off_values", "<i8")],
                align=True)
 BIN = np.dtype([("head_off", "<u4"), ("head_bytes", "<u4"), ("first_tree", "<i4"), ("width", "<i4"),
                 ("phead_off", "<u4"), ("stride", "<i4"), ("nranks", "<i4"), ("nexits", "<i4")])
@@ -34,6 +35,8 @@ class Image:
         self.sthr = deep.view("<f4").reshape(-1, 8)[:, :3]  # thresholds of v, left, right
         dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 16 * g["n_super"]].view("<i4")
         self.deep_leaf = dl.reshape(-1, 4)
+        # forests with leaf values: a leaf reference names a slot of this table
+        self.values = img[g["off_values"]: g["off_values"] + 4 * g["n_values"]].view("<f4")
 
     def head(self, b: int):
         """(thr [nranks][stride], meta [nranks][stride], exits [nexits][stride],

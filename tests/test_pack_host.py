@@ -286,3 +286,30 @@ def test_null_arguments_rejected():
     L.fp_release(None)
     L.fp_release_packed(None)
     L.fp_plain_release(None)
+
+
+@pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 0), (3, 6, 0), (2, 9, 1)])
+def test_value_forest_records_decode_to_oracle(B, d, sel):
+    """A forest with leaf values: every leaf reference names a value slot
+    holding the leaf's value, and the walk reaches the oracle's leaves."""
+    import datagen
+    X, y = datagen.gen_regression(21, 2000, 0, 1.0, 1.0)
+    F = datagen.train_regression(X, y, 6, mtry=9, min_leaf=3, seed=21, threads=4)
+    Xt, _ = datagen.gen_regression(21, 1500, 1, 1.0, 1.0)
+    ref = oracle.predict_values(F, Xt)
+    im = Image(fp.fp_pack_forest(F, bin_size=B, interleave_depth=d, head_select=sel).image())
+    assert im.h["n_values"] == int((F.left < 0).sum())
+    leaf, slot = im.walk(Xt)
+    np.testing.assert_array_equal(leaf, ref["leaf"])
+    np.testing.assert_array_equal(im.values[slot], F.leaf_value[F.node_begin[:-1][None, :] + ref["leaf"]])
+
+
+def test_value_forest_rejects_non_finite_values():
+    import datagen
+    X, y = datagen.gen_regression(22, 500, 0, 1.0, 1.0)
+    F = datagen.train_regression(X, y, 2, mtry=9, min_leaf=3, seed=22, threads=2)
+    F.leaf_value = F.leaf_value.copy()
+    F.leaf_value[np.flatnonzero(F.left < 0)[3]] = np.inf
+    with pytest.raises(fp.FPError) as ei:
+        fp.fp_pack_forest(F)
+    assert ei.value.code == fp.FP_EINVAL
