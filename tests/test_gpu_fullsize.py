@@ -89,3 +89,35 @@ def test_hbm_workload_full_size(layout):
 @pytest.mark.parametrize("layout", [None, (16, 5, 1), (2, 8, 0)])
 def test_image_workload_full_size(layout):
     _run("image", datagen.RECIPES["image"]["n_test"], layout)
+
+
+def _run_values(name, layout, launch):
+    """Value workloads at full size: every row's output is finite, a seeded
+    sample matches the oracle within the float32 bound, leaves exactly."""
+    forest, X, Xd = _data(name, datagen.RECIPES[name]["n_test"])
+    n = X.shape[0]
+    df = fp.fp_upload(fp.fp_pack_forest(forest, **dict(zip(at.LAYOUT_KEYS, layout))))
+    df.configure(**dict(zip(at.LAUNCH_KEYS, launch)))
+    out = df.predict_values(Xd)
+    torch.cuda.synchronize()
+    assert df.sync_status() == fp.FP_OK
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(o))
+    rng = np.random.Generator(np.random.PCG64(4321))
+    idx = np.sort(rng.choice(n, size=min(SAMPLE, n), replace=False))
+    idx[-1] = n - 1
+    ref = oracle.predict_values(forest, X[idx], threads=oracle.default_threads())
+    assert np.all(np.abs(o[idx] - ref["out"]) <= oracle.value_tolerance(forest, ref["abs"]))
+    leaves = df.predict_leaves(torch.from_numpy(np.ascontiguousarray(X[idx])).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
+    df.release()
+
+
+@pytest.mark.parametrize("name", ["regress", "boosted"])
+def test_value_workloads_full_size(name):
+    from bench import TUNE
+    layouts, launches = TUNE[name]
+    for layout in layouts[:2]:
+        for launch in launches[:2]:
+            _run_values(name, layout, launch)
