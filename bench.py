@@ -69,14 +69,14 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-HBM_LAYOUTS = [(4, 9, 1), (3, 9, 1), (2, 9, 1), (3, 8, 1), (1, 10, 1), (16, 5, 1), (3, 8, 0)]  # (B, d, head_select)
-HBM_LAUNCHES = [(768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3), (1024, 32, 16, 3)]  # tile, warps, refill, buffers
+HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (1, 11, 2), (4, 9, 1), (2, 9, 1), (3, 8, 1), (3, 8, 0)]  # (B, d, head_select)
+HBM_LAUNCHES = [(768, 32, 8, 2), (768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3)]  # tile, warps, refill, buffers
 # the value workloads: the regression forest's trees resemble the hbm ones; the
 # boosted trees (depth <= 6) fit whole in a level head of depth 5
 TUNE = {
     "hbm": (HBM_LAYOUTS, HBM_LAUNCHES),
-    "regress": ([(4, 9, 1), (2, 9, 1), (3, 8, 1), (16, 5, 1)], HBM_LAUNCHES),
-    "boosted": ([(16, 5, 1), (32, 5, 1), (8, 5, 1), (64, 5, 1)],
+    "regress": ([(4, 9, 2), (3, 9, 2), (4, 9, 1), (3, 8, 1)], HBM_LAUNCHES),
+    "boosted": ([(64, 5, 2), (32, 5, 2), (64, 5, 1), (16, 5, 1)],
                 [(768, 32, 16, 3), (1024, 32, 16, 3), (512, 16, 16, 3), (1024, 32, 32, 2)]),
 }
 
@@ -217,6 +217,18 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); the value
+    itself with one rank."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def base_line(args, ws, value, total_ms, config, dtype="f32"):
     return {"metric": METRIC, "value": value, "unit": "observations/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -351,11 +363,7 @@ def run_packed(args, ws, rank, local):
     clk = clocks.stop()
     total_ms = start.elapsed_time(stop)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     value = ws * n * args.steps / (total_ms / 1e3)
 
     # plain breadth-first baseline, both thread orders, same inputs

@@ -100,7 +100,9 @@ typedef struct fp_forest_desc {
  *                     popular paths of Section III-A), walked by explicit
  *                     targets; 1 = levels 0..d in implicit breadth-first
  *                     slots (the Bin layout's interleaved levels; every walk
- *                     takes d+1 steps)
+ *                     takes d+1 steps); 2 = the same levels stored two per
+ *                     16-byte record (a node and its children; d odd), one
+ *                     shared-memory load per two levels
  *   bin_buffers       shared-memory buffers that bin blocks stream through,
  *                     2 or 3 (0 = 3): two leave room for larger heads or
  *                     tiles, three hide copy latency better */

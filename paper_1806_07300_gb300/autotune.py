@@ -25,24 +25,30 @@ _SEARCH_VERSION = "levels-v5-nbuf"  # cached results of an older search space ar
 LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")
 
 
-def block_bytes(bin_size: int, depth: int) -> int:
-    """Size of a bin's interleaved block when every tree fills its head."""
+def block_bytes(bin_size: int, depth: int, head_select: int = 1) -> int:
+    """Size of a bin's interleaved block when every tree fills its head
+    (paired level heads: (4^J - 1)/3 records of 16 bytes, J = (d+1)/2)."""
     stride = bin_size | 1
     k = (1 << (depth + 1)) - 1
+    if head_select == 2:
+        return stride * (k // 3) * 16 + stride * (k + 1) * 4
     return stride * k * 8 + stride * (k + 1) * 4
 
 
 def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int = 10) -> list[tuple[int, int, int]]:
     """(B, d, head_select) triples to try: for each bin size, level heads
     (head_select 1) as deep as the block limit allows and one level
-    shallower, and the ranked head of the deepest fitting d."""
+    shallower, paired level heads (head_select 2, d odd) as deep as fits, and
+    the ranked head of the deepest fitting d."""
     out = []
     for B in (1, 2, 3, 5, 8, 16, 32, 64, 128):
         if B > n_trees and out:
             break
         B = min(B, n_trees)
         dmax = max(d for d in range(12) if block_bytes(B, d) <= limit or d == 0)
-        for cand in ((B, dmax, 1), (B, max(0, dmax - 1), 1), (B, min(dmax, 9), 0)):
+        odd = [d for d in (1, 3, 5, 7, 9, 11) if block_bytes(B, d, 2) <= limit]
+        paired = [(B, max(odd), 2)] if odd else []
+        for cand in [(B, dmax, 1), (B, max(0, dmax - 1), 1)] + paired + [(B, min(dmax, 9), 0)]:
             if cand not in out:
                 out.append(cand)
     # spread the picks over bin sizes when trimming
@@ -55,7 +61,7 @@ def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int 
 def candidate_launches(default_tile: int) -> list[tuple[int, int, int, int]]:
     """(obs_tile, warps_per_cta, refill_lanes, bin_buffers) tuples."""
     tiles = sorted({default_tile, max(32, default_tile // 2 // 32 * 32)}, reverse=True)
-    return [(t, w, r, nb) for t in tiles for w in (32, 16) for r in (32, 16) for nb in (3, 2)]
+    return [(t, w, r, nb) for t in tiles for w in (32, 16) for r in (16, 8) for nb in (3, 2)]
 
 
 def forest_key(forest) -> str:

@@ -31,6 +31,14 @@
 // d+1 steps.  Head node {float thr; uint32 meta}, meta[31:22] = feature, the
 // rest zero.  d <= FP_MAX_LEVEL_DEPTH.
 //
+// head_select = 2, paired levels: the same levels, slots and exits, stored two
+// levels per 16-byte record (d odd): record q of super-level j holds the node
+// at level 2j, position p = q - (4^j - 1)/3, and its two children --
+// {thr, thr of left child, thr of right child, features [9:0] node,
+// [19:10] left child, [29:20] right child} -- and its successors are the
+// records 4q+1 .. 4q+4; nranks = (4^J - 1)/3 records for J = (d+1)/2, and
+// record index nranks + e is exit e.
+//
 // head_select = 0, ranked: the K = 2^(d+1) - 1 internal nodes of highest
 // training cardinality (ties: shallower, then earlier), a subtree that
 // contains the root; for a complete tree these are exactly levels 0..d.

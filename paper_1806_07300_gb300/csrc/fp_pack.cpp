@@ -8,8 +8,10 @@
 //        (node[slot*stride + k]), so the roots of all trees of a bin are
 //        contiguous (Fig. 2: depth 0 = roots only) and the block is staged
 //        into shared memory in one piece.  A head is either levels 0..d in
-//        implicit breadth-first slots (the paper's interleaved levels) or the
-//        2^(d+1)-1 most frequently visited nodes of the tree, ranked;
+//        implicit breadth-first slots (the paper's interleaved levels; one
+//        8-byte node per slot, or, paired, a node and its two children per
+//        16-byte slot) or the 2^(d+1)-1 most frequently visited nodes of the
+//        tree, ranked;
 //   DF-  (Section III-A): leaves are not stored as nodes; a reference to a
 //        leaf carries its class (the paper's shared per-class nodes, folded
 //        into the reference so no load is spent on them);
@@ -331,7 +333,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     int32_t B = p.bin_size ? p.bin_size : 1;
     const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
     const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
-    const bool select_levels = p.head_select == 1;
+    const bool select_levels = p.head_select >= 1;  // level heads: single or paired slots
+    const bool paired = p.head_select == 2;
     int32_t R = p.obs_tile;
     if (R == 0) {  // rows take up to ~96 KiB of shared memory
         int64_t r = (96 * 1024) / ((int64_t)F * 4);
@@ -341,7 +344,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
     if (B < 1 || B > 1024 || d < 0 || d > (select_levels ? FP_MAX_LEVEL_DEPTH : FP_MAX_DEPTH) || W < 1 || W > 32 ||
         R < 32 || R > 2048 || R % 32 ||
-        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 1 ||
+        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 2 || (paired && d % 2 == 0) ||
         (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) || p.reserved != 0) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
                      "refill %d, head_select %d, bin_buffers %d)", B, d, R, W, refill, p.head_select,
@@ -402,7 +405,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.n_trees = T; h.n_features = F; h.n_classes = C;
         h.bin_size = B; h.depth = d; h.n_bins = n_bins;
         h.head_nodes = K;
-        h.head_select = select_levels ? 1 : 0;
+        h.head_select = p.head_select;
         h.obs_tile = R; h.warps_per_cta = W;
         h.refill_lanes = refill;
         h.bin_buffers = p.bin_buffers ? p.bin_buffers : 3;
@@ -420,12 +423,14 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                                                                                   : lays[bn.first_tree + k].head.size()));
                 bn.nexits = std::max<int32_t>(bn.nexits, (int32_t)lays[bn.first_tree + k].exits.size());
             }
+            if (paired) bn.nranks = (int32_t)(((int64_t)1 << (d + 1)) - 1) / 3;  // (4^J - 1)/3 paired slots
             if (!select_levels && bn.nranks + bn.nexits > (int32_t)FP_TARGET_MASK + 1) {
                 fp_set_error("fp_pack_forest: bin %d needs %d head targets (at most %u); lower interleave_depth", b,
                              bn.nranks + bn.nexits, FP_TARGET_MASK + 1);
                 return FP_EUNSUPPORTED;
             }
-            const int64_t bytes = align_up((int64_t)bn.nranks * bn.stride * 8 + (int64_t)bn.nexits * bn.stride * 4, 16);
+            const int64_t rec = paired ? 16 : 8;
+            const int64_t bytes = align_up((int64_t)bn.nranks * bn.stride * rec + (int64_t)bn.nexits * bn.stride * 4, 16);
             if (head_total + bytes > UINT32_MAX || bytes > 100 * 1024) {
                 fp_set_error("fp_pack_forest: interleaved block of %lld bytes per bin is too large; lower "
                              "bin_size or interleave_depth", (long long)bytes);
@@ -496,7 +501,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         for (int32_t b = 0; b < n_bins; ++b) {
             const FpBin &bn = bins[b];
             uint8_t *blk = img + h.off_heads + bn.head_off;
-            uint32_t *exits = reinterpret_cast<uint32_t *>(blk + (int64_t)bn.nranks * bn.stride * 8);
+            uint32_t *exits = reinterpret_cast<uint32_t *>(blk + (int64_t)bn.nranks * bn.stride * (paired ? 16 : 8));
             int32_t *pexits = reinterpret_cast<int32_t *>(img + h.off_pheads + bn.phead_off);
             for (int64_t i = 0; i < (int64_t)bn.nexits * bn.stride; ++i) {
                 exits[i] = FP_REF_LEAF | 0x7FFFFFFFu;  // unused entries name no class
@@ -508,6 +513,32 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 TreeRef tr{desc->left + nb, desc->right + nb, desc->feature + nb, desc->leaf_class + nb,
                            desc->threshold + nb, nullptr, desc->tree_node_begin[t + 1] - nb};
                 const TreeLayout &lay = lays[t];
+                if (paired) {
+                    // paired slot q of super-level j (q - (4^j - 1)/3 = p) holds the node at
+                    // level 2j, position p, and its two children; its four successors are
+                    // 4q+1 .. 4q+4, so the walk takes two levels per 16-byte record
+                    int64_t q = 0;
+                    for (int64_t j = 0; q < bn.nranks; ++j) {
+                        const int64_t count = (int64_t)1 << (2 * j);
+                        for (int64_t pos = 0; pos < count; ++pos, ++q) {
+                            const int64_t s = (((int64_t)1 << (2 * j)) - 1) + pos;  // binary slot of the node
+                            const int32_t vv[3] = {lay.slot[s], lay.slot[2 * s + 1], lay.slot[2 * s + 2]};
+                            uint32_t w[4] = {0, 0, 0, 0};
+                            for (int c = 0; c < 3; ++c) {
+                                if (tr.leaf(vv[c])) continue;  // dummy: any outcome lands on the same leaf
+                                memcpy(&w[c], &tr.Th[vv[c]], 4);
+                                w[3] |= (uint32_t)tr.Fe[vv[c]] << (10 * c);
+                            }
+                            memcpy(blk + (q * bn.stride + k) * 16, w, 16);
+                        }
+                    }
+                    for (size_t e = 0; e < lay.exits.size(); ++e) {
+                        const int32_t v = lay.exits[e];
+                        exits[(int64_t)e * bn.stride + k] = ref_of(tr, lay, v, tree_base[t]);
+                        pexits[(int64_t)e * bn.stride + k] = tr.leaf(v) ? v : -1;
+                    }
+                    continue;
+                }
                 if (select_levels) {
                     for (size_t s = 0; s < lay.slot.size(); ++s) {
                         const int32_t v = lay.slot[s];

@@ -18,8 +18,9 @@
 //        burst -- the warp claims 32 consecutive tasks (32 rows of one tree)
 //                 and all lanes walk their paths through the tree's head in
 //                 shared memory together, with a branch-free step (level
-//                 heads: exactly d+1 steps over implicit slots; ranked heads:
-//                 until the last lane leaves the head); paths that leave the
+//                 heads: exactly d+1 steps over implicit slots, or (d+1)/2
+//                 steps of two levels when the slots are paired; ranked
+//                 heads: until the last lane leaves the head); paths that leave the
 //                 head are pushed, compacted with __ballot_sync / __popc,
 //                 into the warp's ring of pending tasks;
 //        deep  -- every lane holding a task resolves two more levels with one
@@ -69,7 +70,7 @@ struct TravParams {
     int32_t n_passes;
     int32_t head_smem;        // bytes reserved for one bin block
     int32_t nbuf;             // bin-block buffers (2 or 3)
-    int32_t levels;           // 1: level heads (implicit slots, depth+1 steps); 0: ranked heads
+    int32_t levels;           // head kind: 0 ranked, 1 level slots (depth+1 steps), 2 paired level slots
     int32_t depth;            // d of the interleaved head
     int32_t refill;           // bursts start when the ring holds at most this many tasks
     uint32_t *out_votes;      // single pass: final votes (may be NULL)
@@ -407,7 +408,8 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         const int ntask = rows * bn.width;
         const uint8_t *blk = hbuf0 + buf * p.head_smem;
         const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
-        const uint32_t *hexit = reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * 8);
+        const uint32_t *hexit =
+            reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * (p.levels == 2 ? 16 : 8));
 
         for (;;) {
             uint32_t w[8];
@@ -417,7 +419,11 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&sh.task_next[buf], 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= ntask) break;  // the bin is claimed out; the step above is issued again later
+                if (base >= ntask) {  // the bin is claimed out: use the load in flight, then move on
+                    if (L.active) deep_finish<MODE>(p, xs, svotes, row0, L, w);
+                    pop_tasks(p, ring, head, tail, L, lt_mask);
+                    break;
+                }
                 const bool my = lane < ntask - base;
                 const int task = base + lane;
                 // task / rows by a float reciprocal, corrected to the exact quotient
@@ -430,7 +436,20 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
                 const float *xr = xs + r2;     // this lane's row
-                if (p.levels) {
+                if (p.levels == 2) {
+                    // paired slots: a node and its two children per 16-byte record,
+                    // successors 4q+1 .. 4q+4; (depth+1)/2 records per walk
+                    const uint4 *hq = reinterpret_cast<const uint4 *>(blk) + k2;
+                    for (int l = 0; l <= p.depth; l += 2) {
+                        const uint4 nd = hq[hr * stride];
+                        const float x0 = xr[(nd.w & 1023u) * R];
+                        const uint32_t d0 = x0 <= __uint_as_float(nd.x) ? 0u : 1u;
+                        const uint32_t f1 = d0 ? (nd.w >> 20) & 1023u : (nd.w >> 10) & 1023u;
+                        const float x1 = xr[f1 * R];
+                        const uint32_t d1 = x1 <= __uint_as_float(d0 ? nd.z : nd.y) ? 0u : 1u;
+                        hr = 4 * hr + 1 + 2 * d0 + d1;
+                    }
+                } else if (p.levels) {
                     // implicit slots: every walk takes depth+1 steps, children 2s+1, 2s+2
                     for (int l = 0; l <= p.depth; ++l) {
                         const uint2 nd = hn[hr * stride];

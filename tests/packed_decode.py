@@ -40,14 +40,21 @@ class Image:
 
     def head(self, b: int):
         """(thr [nranks][stride], meta [nranks][stride], exits [nexits][stride],
-        exit leaf ids [nexits][stride]) of bin b's interleaved block."""
+        exit leaf ids [nexits][stride]) of bin b's interleaved block; for
+        paired level heads thr is [nranks][stride][3] (node, left and right
+        child) and meta [nranks][stride] the packed features."""
         g, bn = self.h, self.bins[b]
         st, nr, ne = int(bn["stride"]), int(bn["nranks"]), int(bn["nexits"])
         base = g["off_heads"] + int(bn["head_off"])
-        recs = self.img[base: base + 8 * nr * st]
-        thr = recs.view("<f4")[0::2].reshape(nr, st)
-        meta = recs.view("<u4")[1::2].reshape(nr, st)
-        exits = self.img[base + 8 * nr * st: base + 8 * nr * st + 4 * ne * st].view("<u4").reshape(ne, st)
+        rec = 16 if g["head_select"] == 2 else 8
+        recs = self.img[base: base + rec * nr * st]
+        if rec == 16:
+            thr = recs.view("<f4").reshape(nr, st, 4)[:, :, :3]
+            meta = recs.view("<u4").reshape(nr, st, 4)[:, :, 3]
+        else:
+            thr = recs.view("<f4")[0::2].reshape(nr, st)
+            meta = recs.view("<u4")[1::2].reshape(nr, st)
+        exits = self.img[base + rec * nr * st: base + rec * nr * st + 4 * ne * st].view("<u4").reshape(ne, st)
         pb = g["off_pheads"] + int(bn["phead_off"])
         par = self.img[pb: pb + 4 * ne * st].view("<i4").reshape(ne, st)
         return thr, meta, exits, par
@@ -72,7 +79,16 @@ class Image:
                         m = meta[hr, k].astype(np.int64)
                         right = ~(X[rows, m >> 22] <= thr[hr, k])
                         hr = 2 * hr + 1 + right
-                busy = np.full(n, g["head_select"] != 1)
+                elif g["head_select"] == 2:  # paired records: successors 4q+1 .. 4q+4
+                    assert nr == (4 ** ((g["depth"] + 1) // 2) - 1) // 3
+                    for _ in range((g["depth"] + 1) // 2):
+                        m = meta[hr, k].astype(np.int64)
+                        th = thr[hr, k]
+                        d0 = ~(X[rows, m & 1023] <= th[:, 0])
+                        f1 = np.where(d0, (m >> 20) & 1023, (m >> 10) & 1023)
+                        d1 = ~(X[rows, f1] <= np.where(d0, th[:, 2], th[:, 1]))
+                        hr = 4 * hr + 1 + 2 * d0 + d1
+                busy = np.full(n, g["head_select"] == 0)
                 while np.any(busy):
                     a = rows[busy]
                     m = meta[hr[a], k].astype(np.int64)

@@ -13,22 +13,25 @@ def test_block_bytes_formula():
     assert at.block_bytes(1, 0) == 1 * 1 * 8 + 1 * 2 * 4
     assert at.block_bytes(2, 1) == 3 * 3 * 8 + 3 * 4 * 4
     assert at.block_bytes(16, 3) == 17 * 15 * 8 + 17 * 16 * 4
+    # paired level heads: (4^2 - 1)/3 = 5 records of 16 bytes and 16 exits per tree slot
+    assert at.block_bytes(16, 3, 2) == 17 * 5 * 16 + 17 * 16 * 4
 
 
 def test_candidate_layouts_pack(tiny_forest):
     cands = at.candidate_layouts(tiny_forest.n_trees)
     assert 2 <= len(cands) <= 10
-    assert {sel for _, _, sel in cands} == {0, 1}
+    assert {sel for _, _, sel in cands} >= {0, 1}
     for B, d, sel in cands:
         assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (11 if sel else 9)
-        assert at.block_bytes(B, d) <= 48 * 1024 or d == 0
+        assert at.block_bytes(B, d, sel) <= 48 * 1024 or d == 0
+        assert sel != 2 or d % 2 == 1
         fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
 
 
 def test_candidate_launches():
     for tile, warps, refill, nbuf in at.candidate_launches(480):
         assert tile % 32 == 0 and 32 <= tile <= 480
-        assert warps in (16, 32) and refill in (16, 32) and nbuf in (2, 3)
+        assert warps in (16, 32) and refill in (8, 16) and nbuf in (2, 3)
 
 
 def test_forest_key_changes_with_forest(tiny_forest):

@@ -46,8 +46,10 @@ def test_batched_mixed_layouts_and_passes(tiny_forest, tiny_rows):
               dict(bin_size=3, interleave_depth=5, pass_bytes=1),
               dict(bin_size=8, interleave_depth=4, head_select=1, bin_buffers=2),
               dict(bin_size=2, interleave_depth=6, head_select=1, pass_bytes=4096, bin_buffers=2),
-              dict(bin_size=3, interleave_depth=3, pass_bytes=2048, bin_buffers=2)]
-    sizes = [1, 777, 31, 4096, 2500, 1500, 999, 3333]
+              dict(bin_size=3, interleave_depth=3, pass_bytes=2048, bin_buffers=2),
+              dict(bin_size=4, interleave_depth=5, head_select=2), dict(bin_size=2, interleave_depth=7, head_select=2,
+                                                                         pass_bytes=8192, bin_buffers=2)]
+    sizes = [1, 777, 31, 4096, 2500, 1500, 999, 3333, 2049, 640]
     forests = [fp.fp_upload(fp.fp_pack_forest(tiny_forest, **p)) for p in params]
     Xh = [X[i * 7: i * 7 + n] for i, n in enumerate(sizes)]
     Xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in Xh]

@@ -40,7 +40,7 @@ def test_binding_has_no_cpu_path():
 
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 0, 0), (2, 1, 0), (3, 2, 0), (1, 5, 0), (1, 0, 1), (2, 1, 1),
-                                     (3, 4, 1)])
+                                     (3, 4, 1), (1, 1, 2), (2, 3, 2)])
 def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
     forest, X, exp = load(name)
     pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel)
@@ -49,7 +49,7 @@ def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
 
 
 @pytest.mark.parametrize("B,d,sel", [(16, 4, 0), (5, 0, 0), (1, 2, 0), (7, 7, 0), (16, 4, 1), (3, 0, 1), (1, 9, 1),
-                                     (1, 11, 1)])
+                                     (1, 11, 1), (3, 1, 2), (4, 9, 2), (1, 11, 2), (16, 5, 2)])
 def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel):
     X, _ = tiny_rows
     ref = oracle.predict(tiny_forest, X[:3000])
@@ -269,8 +269,9 @@ def test_unsupported_sizes_rejected():
 
 
 @pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(interleave_depth=12, head_select=1),
-                                dict(obs_tile=33), dict(warps_per_cta=40), dict(head_select=2),
-                                dict(bin_buffers=1), dict(bin_buffers=4)])
+                                dict(obs_tile=33), dict(warps_per_cta=40),
+                                dict(bin_buffers=1), dict(bin_buffers=4), dict(head_select=2, interleave_depth=8),
+                                dict(head_select=3)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(tiny_forest, **kw)
