@@ -69,7 +69,7 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (1, 11, 2), (4, 9, 1), (2, 9, 1), (3, 8, 1), (3, 8, 0)]  # (B, d, head_select)
+HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (1, 11, 2), (4, 9, 1), (2, 9, 1), (3, 8, 1), (3, 8, 3)]  # (B, d, head_select)
 HBM_LAUNCHES = [(768, 32, 8, 2), (768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3)]  # tile, warps, refill, buffers
 # the value workloads: the regression forest's trees resemble the hbm ones; the
 # boosted trees (depth <= 6) fit whole in a level head of depth 5
@@ -95,7 +95,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--bin-size", type=int, default=0)
     ap.add_argument("--depth", type=int, default=-1)
-    ap.add_argument("--head-select", type=int, default=1, help="1: levels 0..d (implicit slots); 0: ranked")
+    ap.add_argument("--head-select", type=int, default=0,
+                    help="0: default; 1: levels 0..d (implicit slots); 2: paired level slots; 3: ranked")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
@@ -496,14 +497,7 @@ def run_batched(args, ws, rank, local):
     sizes = datagen.batch_sizes()
     Xh = [datagen.test_rows(nm, s)[0] for nm, s in zip(names, sizes)]
     Xs = [torch.from_numpy(x).to(dev) for x in Xh]
-    dfs = []
-    for f, x in zip(forests, Xs):
-        if x.shape[0] >= 4096:
-            d, _ = at.upload_tuned(f, x, layouts=at.candidate_layouts(f.n_trees, max_layouts=4),
-                                   launches=[(0, 32, 32)])
-        else:
-            d = fp.fp_upload(fp.fp_pack_forest(f))
-        dfs.append(d)
+    dfs, tuning = at.autotune_batched(forests, Xs)  # one layout for the shared launch
     votes = [torch.empty((x.shape[0], f.n_classes), dtype=torch.int32, device=dev) for f, x in zip(forests, Xs)]
     cls = [torch.empty((x.shape[0],), dtype=torch.int32, device=dev) for x in Xs]
     stream = torch.cuda.Stream(device=dev)
@@ -534,6 +528,7 @@ def run_batched(args, ws, rank, local):
     out = base_line(args, ws, value, total_ms,
                     {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
                      "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
+                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "launch")},
                      "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
     out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
                 "e2e": None, "roofline": None, "cpu_baseline": None})
@@ -655,9 +650,9 @@ def run_ablation(args, ws, rank, local):
         ("Stat (training cardinalities), roots only", forest, dict(bin_size=1, interleave_depth=0), {}),
         ("Stat (counted on 200k observations), roots only", inferred, dict(bin_size=1, interleave_depth=0), {}),
         ("Bin B=16, levels 0..4", forest, dict(bin_size=16, interleave_depth=4, head_select=1), {}),
-        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4, head_select=0), {}),
+        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4, head_select=3), {}),
         ("Bin B=3, levels 0..8", forest, dict(bin_size=3, interleave_depth=8, head_select=1), {}),
-        ("Bin B=3, 511 most visited nodes", forest, dict(bin_size=3, interleave_depth=8, head_select=0), {}),
+        ("Bin B=3, 511 most visited nodes", forest, dict(bin_size=3, interleave_depth=8, head_select=3), {}),
         ("autotuned", forest, {k: best[k] for k in at.LAYOUT_KEYS}, {k: best[k] for k in at.LAUNCH_KEYS}),
     ]
     for label, f, params, launch in variants:

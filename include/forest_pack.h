@@ -82,10 +82,11 @@ typedef struct fp_forest_desc {
 /* Layout and launch parameters; 0 selects the default (for interleave_depth,
  * -1 does, since 0 is a valid depth).
  *   bin_size          B, trees per bin (Section III-A "stripe width"), 1..1024
+ *                     (default 3)
  *   interleave_depth  d: each tree contributes 2^(d+1)-1 nodes (levels 0..d of
  *                     a complete tree) to its bin's interleaved block
  *                     (Section III-A), 0..9 for ranked heads, 0..11 for
- *                     level heads
+ *                     level heads (default 9)
  *   obs_tile          observations per work item of the traversal kernel,
  *                     a multiple of 32, up to 2048
  *   warps_per_cta     warps per CTA of the traversal kernel, 1..32
@@ -96,13 +97,14 @@ typedef struct fp_forest_desc {
  *   refill_lanes      a warp hands new (observation, tree) tasks to its idle
  *                     lanes once this many lanes are idle, 1..32
  *   head_select       which 2^(d+1)-1 nodes of a tree form its interleaved head:
- *                     0 = ranked: those of highest training cardinality (the
- *                     popular paths of Section III-A), walked by explicit
- *                     targets; 1 = levels 0..d in implicit breadth-first
- *                     slots (the Bin layout's interleaved levels; every walk
- *                     takes d+1 steps); 2 = the same levels stored two per
- *                     16-byte record (a node and its children; d odd), one
- *                     shared-memory load per two levels
+ *                     1 = levels 0..d in implicit breadth-first slots (the
+ *                     Bin layout's interleaved levels; every walk takes d+1
+ *                     steps); 2 = the same levels stored two per 16-byte
+ *                     record (a node and its children; d odd), one
+ *                     shared-memory load per two levels; 3 = ranked: the
+ *                     nodes of highest training cardinality (the popular
+ *                     paths of Section III-A), walked by explicit targets;
+ *                     0 = default: 2 when d is odd, else 1
  *   bin_buffers       shared-memory buffers that bin blocks stream through,
  *                     2 or 3 (0 = 3): two leave room for larger heads or
  *                     tiles, three hide copy latency better */

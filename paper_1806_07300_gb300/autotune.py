@@ -21,7 +21,7 @@ from . import FPError, fp_pack_forest, fp_predict, fp_predict_values, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
 LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select")
-_SEARCH_VERSION = "levels-v5-nbuf"  # cached results of an older search space are not reused
+_SEARCH_VERSION = "heads-v6"  # cached results of an older search space are not reused
 LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")
 
 
@@ -39,7 +39,7 @@ def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int 
     """(B, d, head_select) triples to try: for each bin size, level heads
     (head_select 1) as deep as the block limit allows and one level
     shallower, paired level heads (head_select 2, d odd) as deep as fits, and
-    the ranked head of the deepest fitting d."""
+    the ranked head (head_select 3) of the deepest fitting d."""
     out = []
     for B in (1, 2, 3, 5, 8, 16, 32, 64, 128):
         if B > n_trees and out:
@@ -48,7 +48,7 @@ def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int 
         dmax = max(d for d in range(12) if block_bytes(B, d) <= limit or d == 0)
         odd = [d for d in (1, 3, 5, 7, 9, 11) if block_bytes(B, d, 2) <= limit]
         paired = [(B, max(odd), 2)] if odd else []
-        for cand in [(B, dmax, 1), (B, max(0, dmax - 1), 1)] + paired + [(B, min(dmax, 9), 0)]:
+        for cand in [(B, dmax, 1), (B, max(0, dmax - 1), 1)] + paired + [(B, min(dmax, 9), 3)]:
             if cand not in out:
                 out.append(cand)
     # spread the picks over bin sizes when trimming
@@ -137,7 +137,7 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
     ref = None
     for lay in layouts:
         B, d = lay[0], lay[1]
-        sel = lay[2] if len(lay) > 2 else 0
+        sel = lay[2] if len(lay) > 2 else 0  # 0: the library's default head kind
         t0 = time.perf_counter()
         try:
             df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel))
@@ -191,3 +191,61 @@ def upload_tuned(forest, X, **kw):
     df = fp_upload(fp_pack_forest(forest, **{k: best[k] for k in LAYOUT_KEYS}))
     df.configure(**{k: best[k] for k in LAUNCH_KEYS})
     return df, best
+
+
+BATCHED_LAYOUTS = [(3, 9, 2), (8, 7, 2), (4, 8, 1), (16, 5, 2)]
+BATCHED_LAUNCHES = [(0, 32, 16, 3), (0, 32, 32, 3)]
+
+
+def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -> tuple[list, dict]:
+    """Tune one persistent launch over several forests (fp_predict_batched):
+    every forest gets the same layout and launch parameters, and each
+    candidate is timed as the whole batched call, since the forests share its
+    CTAs (per-forest tuning does not predict the shared launch).  Returns
+    (device forests configured with the best candidate, result dict)."""
+    import torch
+    from . import fp_predict_batched
+    table, best, best_dfs = [], None, None
+    votes = [torch.empty((x.shape[0], f.n_classes), dtype=torch.int32, device=x.device) for f, x in zip(forests, Xs)]
+    cls = [torch.empty((x.shape[0],), dtype=torch.int32, device=x.device) for x in Xs]
+    for B, d, sel in (layouts or BATCHED_LAYOUTS):
+        try:
+            dfs = [fp_upload(fp_pack_forest(f, bin_size=min(B, f.n_trees), interleave_depth=d, head_select=sel))
+                   for f in forests]
+        except FPError as e:
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, error=str(e)))
+            continue
+        for launch in (launches or BATCHED_LAUNCHES):
+            tile, warps, refill, nbuf = launch
+            try:
+                for df in dfs:
+                    df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
+            except FPError as e:
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, launch=launch, error=str(e)))
+                continue
+            fp_predict_batched(dfs, Xs, votes, cls)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fp_predict_batched(dfs, Xs, votes, cls)
+            b.record()
+            torch.cuda.synchronize()
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, launch=list(launch),
+                       ms=a.elapsed_time(b) / reps)
+            table.append(row)
+            if best is None or row["ms"] < best["ms"]:
+                if best_dfs is not None and best_dfs[0] is not dfs:
+                    for df in best_dfs[0]:  # the previous best layout's forests
+                        df.release()
+                best, best_dfs = row, (dfs, launch)
+        if best_dfs is None or best_dfs[0] is not dfs:
+            for df in dfs:
+                df.release()
+    if best is None:
+        raise RuntimeError("autotune_batched: no candidate could run")
+    dfs, launch = best_dfs
+    tile, warps, refill, nbuf = launch
+    for df in dfs:
+        df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
+    return dfs, dict(best, table=table)

@@ -187,7 +187,7 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.n_tiles = (n + f->R - 1) / f->R;
     p.head_smem = f->head_smem;
     p.nbuf = f->nbuf;
-    p.levels = h.head_select;
+    p.levels = h.head_select == 3 ? 0 : h.head_select;  // kernel: 0 ranked, 1 level slots, 2 paired
     p.leaf_val = reinterpret_cast<const float *>(f->d_image + h.off_values);
     p.n_vals = (uint32_t)h.n_values;
     p.depth = h.depth;

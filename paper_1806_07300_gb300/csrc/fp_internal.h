@@ -20,7 +20,8 @@
 //                                [nexits][stride] like the exits
 //   deep_leaf int32[4] per super-node: leaf id behind each exit, or -1
 //
-// Two kinds of head (the header's head_select, the same for every bin):
+// Three kinds of head (the header's head_select, the same for every bin; 1
+// and 2 are the level heads, 3 the ranked one):
 //
 // head_select = 1, levels (the Bin layout of Section III-A): levels 0..d of
 // every tree in implicit breadth-first slots, nranks = 2^(d+1) - 1 and
@@ -39,7 +40,7 @@
 // records 4q+1 .. 4q+4; nranks = (4^J - 1)/3 records for J = (d+1)/2, and
 // record index nranks + e is exit e.
 //
-// head_select = 0, ranked: the K = 2^(d+1) - 1 internal nodes of highest
+// head_select = 3, ranked: the K = 2^(d+1) - 1 internal nodes of highest
 // training cardinality (ties: shallower, then earlier), a subtree that
 // contains the root; for a complete tree these are exactly levels 0..d.
 // They are ranked in depth-first order that visits the more frequently
@@ -107,7 +108,7 @@ struct FpImageHeader {
     int32_t n_trees, n_features, n_classes;
     int32_t bin_size, depth, n_bins, n_passes;
     int32_t head_nodes;            // K, head nodes per tree at most
-    int32_t head_select;           // 0: ranked (highest cardinality), 1: levels 0..d in implicit slots
+    int32_t head_select;           // 1: levels 0..d in implicit slots, 2: paired slots, 3: ranked
     int32_t obs_tile, warps_per_cta;
     int32_t max_head_bytes;
     int32_t refill_lanes;

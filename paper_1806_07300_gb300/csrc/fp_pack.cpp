@@ -330,11 +330,13 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     }
     fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0, 0, 0};
     const int32_t refill = p.refill_lanes ? p.refill_lanes : 32;
-    int32_t B = p.bin_size ? p.bin_size : 1;
+    int32_t B = p.bin_size ? p.bin_size : 3;
     const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
+    // head kind: 0 = default (paired level slots when d is odd, else level slots)
+    const int32_t kind = p.head_select ? p.head_select : (d % 2 ? 2 : 1);
     const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
-    const bool select_levels = p.head_select >= 1;  // level heads: single or paired slots
-    const bool paired = p.head_select == 2;
+    const bool select_levels = kind == 1 || kind == 2;  // level heads: single or paired slots
+    const bool paired = kind == 2;
     int32_t R = p.obs_tile;
     if (R == 0) {  // rows take up to ~96 KiB of shared memory
         int64_t r = (96 * 1024) / ((int64_t)F * 4);
@@ -344,7 +346,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const int64_t pass_budget = p.pass_bytes ? p.pass_bytes : (int64_t)48 << 20;
     if (B < 1 || B > 1024 || d < 0 || d > (select_levels ? FP_MAX_LEVEL_DEPTH : FP_MAX_DEPTH) || W < 1 || W > 32 ||
         R < 32 || R > 2048 || R % 32 ||
-        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 2 || (paired && d % 2 == 0) ||
+        refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 3 || (paired && d % 2 == 0) ||
         (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) || p.reserved != 0) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
                      "refill %d, head_select %d, bin_buffers %d)", B, d, R, W, refill, p.head_select,
@@ -405,7 +407,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.n_trees = T; h.n_features = F; h.n_classes = C;
         h.bin_size = B; h.depth = d; h.n_bins = n_bins;
         h.head_nodes = K;
-        h.head_select = p.head_select;
+        h.head_select = kind;
         h.obs_tile = R; h.warps_per_cta = W;
         h.refill_lanes = refill;
         h.bin_buffers = p.bin_buffers ? p.bin_buffers : 3;

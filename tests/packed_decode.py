@@ -88,7 +88,7 @@ class Image:
                         f1 = np.where(d0, (m >> 20) & 1023, (m >> 10) & 1023)
                         d1 = ~(X[rows, f1] <= np.where(d0, th[:, 2], th[:, 1]))
                         hr = 4 * hr + 1 + 2 * d0 + d1
-                busy = np.full(n, g["head_select"] == 0)
+                busy = np.full(n, g["head_select"] == 3)  # ranked heads: explicit targets
                 while np.any(busy):
                     a = rows[busy]
                     m = meta[hr[a], k].astype(np.int64)

@@ -20,9 +20,9 @@ def test_block_bytes_formula():
 def test_candidate_layouts_pack(tiny_forest):
     cands = at.candidate_layouts(tiny_forest.n_trees)
     assert 2 <= len(cands) <= 10
-    assert {sel for _, _, sel in cands} >= {0, 1}
+    assert {sel for _, _, sel in cands} >= {1, 3}
     for B, d, sel in cands:
-        assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (11 if sel else 9)
+        assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (9 if sel == 3 else 11)
         assert at.block_bytes(B, d, sel) <= 48 * 1024 or d == 0
         assert sel != 2 or d % 2 == 1
         fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
@@ -51,7 +51,7 @@ def test_autotune_tiny_on_gpu(tiny_forest, tiny_rows, tmp_path, monkeypatch):
     monkeypatch.setenv("FP_CACHE_DIR", str(tmp_path))
     X, _ = tiny_rows
     Xd = torch.from_numpy(X).cuda()
-    best = at.autotune(tiny_forest, Xd, layouts=[(1, 3), (16, 4, 1), (4, 6, 0), (2, 7, 1)],
+    best = at.autotune(tiny_forest, Xd, layouts=[(1, 3), (16, 4, 1), (4, 6, 3), (2, 7, 2)],
                        launches=[(256, 16, 16), (128, 32, 32, 2)])
     assert best["ms"] > 0 and len(best["table"]) == 8
     again = at.autotune(tiny_forest, Xd, layouts=[(1, 0)])  # served from the cache
@@ -62,3 +62,22 @@ def test_autotune_tiny_on_gpu(tiny_forest, tiny_rows, tmp_path, monkeypatch):
     ref = oracle.predict(tiny_forest, X)
     np.testing.assert_array_equal(c.cpu().numpy(), ref["cls"])
     np.testing.assert_array_equal(v.cpu().numpy().astype(np.uint32), ref["votes"])
+
+
+@pytest.mark.gpu
+def test_autotune_batched_on_gpu(tiny_forest, tiny_rows):
+    """One layout for a shared batched launch, chosen by timing the launch."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    X, _ = tiny_rows
+    Xh = [X[:3000], X[3000:3007], X[4000:9000]]
+    Xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in Xh]
+    dfs, best = at.autotune_batched([tiny_forest] * 3, Xs, layouts=[(3, 9, 2), (8, 4, 1), (2, 5, 3)],
+                                    launches=[(0, 32, 16, 3), (256, 16, 8, 2)], reps=2)
+    assert best["ms"] > 0 and len(best["table"]) == 6
+    cls = [torch.empty((x.shape[0],), dtype=torch.int32, device="cuda") for x in Xs]
+    fp.fp_predict_batched(dfs, Xs, None, cls)
+    torch.cuda.synchronize()
+    for x, c in zip(Xh, cls):
+        np.testing.assert_array_equal(c.cpu().numpy(), oracle.predict(tiny_forest, x)["cls"])

@@ -42,7 +42,7 @@ def test_batched_mixed_layouts_and_passes(tiny_forest, tiny_rows):
     buffers share CTAs)."""
     X, _ = tiny_rows
     params = [dict(bin_size=1, interleave_depth=0), dict(bin_size=4, interleave_depth=3),
-              dict(bin_size=2, interleave_depth=1, pass_bytes=2048), dict(bin_size=16, interleave_depth=9),
+              dict(bin_size=2, interleave_depth=1, pass_bytes=2048), dict(bin_size=16, interleave_depth=9, head_select=3),
               dict(bin_size=3, interleave_depth=5, pass_bytes=1),
               dict(bin_size=8, interleave_depth=4, head_select=1, bin_buffers=2),
               dict(bin_size=2, interleave_depth=6, head_select=1, pass_bytes=4096, bin_buffers=2),

@@ -86,7 +86,7 @@ def test_hbm_workload_full_size(layout):
     _run("hbm", datagen.RECIPES["hbm"]["n_test"], layout, HBM_LAUNCHES)
 
 
-@pytest.mark.parametrize("layout", [None, (16, 5, 1), (2, 8, 0)])
+@pytest.mark.parametrize("layout", [None, (16, 5, 1), (2, 8, 3)])
 def test_image_workload_full_size(layout):
     _run("image", datagen.RECIPES["image"]["n_test"], layout)
 

@@ -50,7 +50,8 @@ def _check_all(forest, X, ref=None, **params):
 
 
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
-@pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 1, 0), (3, 3, 0), (1, 0, 1), (2, 3, 1), (1, 1, 2), (3, 3, 2)])
+@pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 1, 3), (3, 3, 3), (1, 0, 1), (2, 3, 1), (1, 1, 2), (3, 3, 2),
+                                     (3, 9, 0)])
 def test_hand_fixtures_on_gpu(name, B, d, sel):
     """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs; ranked
     heads (sel 0) and level heads (sel 1)."""
@@ -59,7 +60,7 @@ def test_hand_fixtures_on_gpu(name, B, d, sel):
     _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel)
 
 
-@pytest.mark.parametrize("B,d,sel", [(16, 4, 0), (1, 0, 0), (5, 2, 0), (7, 6, 0), (4, 9, 0), (16, 4, 1), (1, 0, 1),
+@pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (1, 0, 3), (5, 2, 3), (7, 6, 3), (4, 9, 3), (16, 4, 1), (1, 0, 1),
                                      (3, 8, 1), (1, 11, 1), (16, 5, 2), (4, 9, 2), (1, 11, 2), (2, 1, 2)])
 def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel):
     X, _ = tiny_rows
@@ -82,7 +83,7 @@ def test_tiny_two_bin_buffers(tiny_forest, tiny_rows, B, d, sel, nbuf):
 
 
 @pytest.mark.parametrize("pass_bytes", [1, 2048, 8192])
-@pytest.mark.parametrize("sel", [0, 1, 2])
+@pytest.mark.parametrize("sel", [3, 1, 2])
 def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes, sel):
     """Several passes: global accumulation and last-pass argmax."""
     X, _ = tiny_rows
@@ -164,6 +165,6 @@ def test_image_workload_params_grid():
     X, _ = datagen.test_rows("image", 3000)
     ref = oracle.predict(forest, X, threads=oracle.default_threads())
     # rows of 784 features leave little shared memory: tiles shrink to fit
-    for B, d, sel, nb in [(128, 1, 0, 3), (16, 3, 0, 3), (8, 5, 0, 3), (1, 9, 0, 3), (16, 5, 1, 3), (1, 10, 1, 3),
+    for B, d, sel, nb in [(128, 1, 3, 3), (16, 3, 3, 3), (8, 5, 3, 3), (1, 9, 3, 3), (16, 5, 1, 3), (1, 10, 1, 3),
                           (4, 7, 2, 3), (1, 11, 2, 2)]:
         _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, bin_buffers=nb)

@@ -51,7 +51,7 @@ def _check(F, X, ref, exact=False, **params):
     return got
 
 
-@pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 1, 1), (3, 3, 0), (1, 2, 1)])
+@pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 1, 1), (3, 3, 3), (1, 2, 1), (3, 9, 0)])
 def test_values_fixture_on_gpu(B, d, sel):
     F, X, exp = load_values("values_small.txt")
     ref = oracle.predict_values(F, X)
@@ -60,10 +60,10 @@ def test_values_fixture_on_gpu(B, d, sel):
 
 @pytest.mark.parametrize("params", [dict(bin_size=4, interleave_depth=9, head_select=1),
                                     dict(bin_size=8, interleave_depth=5, head_select=1, bin_buffers=2),
-                                    dict(bin_size=3, interleave_depth=8, head_select=0),
+                                    dict(bin_size=3, interleave_depth=8, head_select=3),
                                     dict(bin_size=4, interleave_depth=9, head_select=2, bin_buffers=2),
                                     dict(bin_size=2, interleave_depth=4, head_select=1, pass_bytes=65536),
-                                    dict(bin_size=1, interleave_depth=6, head_select=0, pass_bytes=1,
+                                    dict(bin_size=1, interleave_depth=6, head_select=3, pass_bytes=1,
                                          obs_tile=128)])
 def test_regression_forest_layouts(small_regress, params):
     F, X, ref = small_regress
@@ -111,7 +111,7 @@ def test_plain_baseline_values(small_regress, order):
 
 @pytest.mark.parametrize("name,layout", [("boosted", dict(bin_size=16, interleave_depth=5, head_select=1)),
                                          ("boosted", dict(bin_size=64, interleave_depth=5, head_select=2)),
-                                         ("boosted", dict(bin_size=32, interleave_depth=3, head_select=0)),
+                                         ("boosted", dict(bin_size=32, interleave_depth=3, head_select=3)),
                                          ("regress", dict(bin_size=4, interleave_depth=9, head_select=1))])
 def test_value_workloads(name, layout):
     """The benchmark's value workloads, on 50,000 of their test rows."""

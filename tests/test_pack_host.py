@@ -39,7 +39,7 @@ def test_binding_has_no_cpu_path():
 
 
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
-@pytest.mark.parametrize("B,d,sel", [(1, 0, 0), (2, 0, 0), (2, 1, 0), (3, 2, 0), (1, 5, 0), (1, 0, 1), (2, 1, 1),
+@pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 0, 3), (2, 1, 3), (3, 2, 3), (1, 5, 3), (1, 0, 1), (2, 1, 1),
                                      (3, 4, 1), (1, 1, 2), (2, 3, 2)])
 def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
     forest, X, exp = load(name)
@@ -48,7 +48,7 @@ def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
     np.testing.assert_array_equal(leaf, exp["leaf"])
 
 
-@pytest.mark.parametrize("B,d,sel", [(16, 4, 0), (5, 0, 0), (1, 2, 0), (7, 7, 0), (16, 4, 1), (3, 0, 1), (1, 9, 1),
+@pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (5, 0, 3), (1, 2, 3), (7, 7, 3), (16, 4, 1), (3, 0, 1), (1, 9, 1),
                                      (1, 11, 1), (3, 1, 2), (4, 9, 2), (1, 11, 2), (16, 5, 2)])
 def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel):
     X, _ = tiny_rows
@@ -114,7 +114,7 @@ def test_head_is_top_cardinality_and_stat_ranked(tiny_forest, d):
     Section III-A; within the head the first child visited sits at the next
     rank and is the child of larger cardinality (Stat)."""
     f = tiny_forest
-    im = Image(fp.fp_pack_forest(f, bin_size=3, interleave_depth=d).image())
+    im = Image(fp.fp_pack_forest(f, bin_size=3, interleave_depth=d, head_select=3).image())
     K = 2 ** (d + 1) - 1
     for t in range(f.n_trees):
         tr = f.tree(t)
@@ -174,7 +174,7 @@ def test_stat_order_in_super_nodes(tiny_forest):
     reached child super-node (Section III-A, Stat), and every internal node
     lies in the head or in exactly one super-node."""
     f = tiny_forest
-    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=2)
+    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=2, head_select=3)
     im = Image(pk.image())
     total = 0
     for t in range(f.n_trees):
@@ -204,7 +204,7 @@ def test_head_interleaving_roots_contiguous(tiny_forest):
     """Fig. 2 caption: the roots of a bin's trees sit side by side (rank 0),
     then the trees' next nodes, rank by rank."""
     f = tiny_forest
-    im = Image(fp.fp_pack_forest(f, bin_size=8, interleave_depth=0).image())
+    im = Image(fp.fp_pack_forest(f, bin_size=8, interleave_depth=0, head_select=3).image())
     for b in range(im.h["n_bins"]):
         thr, meta, exits, par = im.head(b)
         assert meta.shape[0] == 1  # d = 0: one node (the root) per tree
@@ -268,10 +268,10 @@ def test_unsupported_sizes_rejected():
     assert ei.value.code == fp.FP_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=10), dict(interleave_depth=12, head_select=1),
+@pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=12), dict(interleave_depth=12, head_select=1),
                                 dict(obs_tile=33), dict(warps_per_cta=40),
                                 dict(bin_buffers=1), dict(bin_buffers=4), dict(head_select=2, interleave_depth=8),
-                                dict(head_select=3)])
+                                dict(head_select=4), dict(head_select=3, interleave_depth=10)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(tiny_forest, **kw)
@@ -289,7 +289,7 @@ def test_null_arguments_rejected():
     L.fp_plain_release(None)
 
 
-@pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 0), (3, 6, 0), (2, 9, 1)])
+@pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 3), (3, 6, 3), (2, 9, 1), (3, 9, 0)])
 def test_value_forest_records_decode_to_oracle(B, d, sel):
     """A forest with leaf values: every leaf reference names a value slot
     holding the leaf's value, and the walk reaches the oracle's leaves."""
