@@ -428,6 +428,7 @@ def run_packed(args, ws, rank, local):
     import oracle
     threads = oracle.default_threads()
     cpu_value, visits_per_obs, m, cpu_s = cpu_sample(forest, Xh, args.cpu_seconds, threads)
+    cpu1_value, _, m1, cpu1_s = cpu_sample(forest, Xh, max(0.5, args.cpu_seconds / 4), 1)  # one core
     # node records, the row, and the outputs (votes and class; or the leaf
     # value read per tree and one float out)
     bytes_per_obs = 8.0 * visits_per_obs + 4.0 * F + (4.0 * T + 4.0 if values else 4.0 * C + 4.0)
@@ -473,7 +474,9 @@ def run_packed(args, ws, rank, local):
         "gpu_launches": args.steps,
         "roofline": roofline,
         "cpu_baseline": {"value": cpu_value, "unit": "observations/s", "cores": threads, "kind": "oracle",
-                         "sample": f"first {m} of {n} rows ({cpu_s:.1f} s)"},
+                         "sample": f"first {m} of {n} rows ({cpu_s:.1f} s)",
+                         "single_core": {"value": cpu1_value, "cores": 1,
+                                         "sample": f"first {m1} of {n} rows ({cpu1_s:.1f} s)"}},
         "clocks": clk,
     })
     print(json.dumps(out))

@@ -183,8 +183,15 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.F = h.n_features;
     p.C = h.n_classes;
     p.T = h.n_trees;
-    p.R = f->R;
-    p.n_tiles = (n + f->R - 1) / f->R;
+    // A small batch gets smaller tiles, so that its (pass, tile) items still
+    // reach every resident CTA; shared memory is laid out for f->R rows and a
+    // smaller tile (a multiple of 32) fits in it.
+    int32_t R = f->R;
+    const int64_t grid = std::max<int64_t>(1, f->grid_votes);
+    const int64_t want = (n * std::max<int32_t>(1, h.n_passes) + grid - 1) / grid;  // rows per tile
+    if (want < R) R = (int32_t)std::max<int64_t>(32, (want + 31) / 32 * 32);
+    p.R = R;
+    p.n_tiles = (n + R - 1) / R;
     p.head_smem = f->head_smem;
     p.nbuf = f->nbuf;
     p.levels = h.head_select == 3 ? 0 : h.head_select;  // kernel: 0 ranked, 1 level slots, 2 paired
