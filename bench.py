@@ -76,6 +76,10 @@ HBM_LAUNCHES = [(768, 32, 8, 2), (768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 
 TUNE = {
     "hbm": (HBM_LAYOUTS, HBM_LAUNCHES),
     "regress": ([(4, 9, 2), (3, 9, 2), (4, 9, 1), (3, 8, 1)], HBM_LAUNCHES),
+    # 784-feature rows fill shared memory with a 32-row tile: small heads and
+    # 16-warp CTAs let two CTAs share an SM
+    "image": ([(16, 3, 2), (16, 1, 2), (8, 3, 1), (64, 4, 3)],
+              [(32, 16, 8, 2), (32, 16, 16, 2), (32, 32, 16, 2), (32, 32, 16, 3)]),
     "boosted": ([(64, 5, 2), (32, 5, 2), (64, 5, 1), (16, 5, 1)],
                 [(768, 32, 16, 3), (1024, 32, 16, 3), (512, 16, 16, 3), (1024, 32, 32, 2)]),
 }

@@ -35,24 +35,29 @@ def block_bytes(bin_size: int, depth: int, head_select: int = 1) -> int:
     return stride * k * 8 + stride * (k + 1) * 4
 
 
-def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int = 10) -> list[tuple[int, int, int]]:
-    """(B, d, head_select) triples to try: for each bin size, level heads
-    (head_select 1) as deep as the block limit allows and one level
-    shallower, paired level heads (head_select 2, d odd) as deep as fits, and
-    the ranked head (head_select 3) of the deepest fitting d."""
+def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int | None = None
+                      ) -> list[tuple[int, int, int]]:
+    """(B, d, head_select) triples to try: for bins of 1, 3, 8, 16 and 64
+    trees, the deepest paired level head (head_select 2, d odd) and the
+    deepest level head (head_select 1) whose block fits the limit, and a
+    small paired head (d = 3), which leaves shared memory to tiles of wide
+    rows or to a second CTA per SM; and one ranked head (head_select 3)."""
     out = []
-    for B in (1, 2, 3, 5, 8, 16, 32, 64, 128):
-        if B > n_trees and out:
-            break
+
+    def add(c):
+        if c not in out:
+            out.append(c)
+
+    for B in (1, 3, 8, 16, 64):
         B = min(B, n_trees)
-        dmax = max(d for d in range(12) if block_bytes(B, d) <= limit or d == 0)
         odd = [d for d in (1, 3, 5, 7, 9, 11) if block_bytes(B, d, 2) <= limit]
-        paired = [(B, max(odd), 2)] if odd else []
-        for cand in [(B, dmax, 1), (B, max(0, dmax - 1), 1)] + paired + [(B, min(dmax, 9), 3)]:
-            if cand not in out:
-                out.append(cand)
-    # spread the picks over bin sizes when trimming
-    if len(out) > max_layouts:
+        if odd:
+            add((B, max(odd), 2))
+        add((B, max(d for d in range(12) if block_bytes(B, d) <= limit or d == 0), 1))
+        add((B, 3, 2))
+    B = min(3, n_trees)
+    add((B, min(9, max(d for d in range(10) if block_bytes(B, d, 3) <= limit or d == 0)), 3))
+    if max_layouts is not None and len(out) > max_layouts:
         idx = np.linspace(0, len(out) - 1, max_layouts).round().astype(int)
         out = [out[i] for i in sorted(set(idx))]
     return out

@@ -19,8 +19,9 @@ def test_block_bytes_formula():
 
 def test_candidate_layouts_pack(tiny_forest):
     cands = at.candidate_layouts(tiny_forest.n_trees)
-    assert 2 <= len(cands) <= 10
-    assert {sel for _, _, sel in cands} >= {1, 3}
+    assert 2 <= len(cands) <= 16
+    assert {sel for _, _, sel in cands} == {1, 2, 3}
+    assert len(at.candidate_layouts(tiny_forest.n_trees, max_layouts=5)) <= 5
     for B, d, sel in cands:
         assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (9 if sel == 3 else 11)
         assert at.block_bytes(B, d, sel) <= 48 * 1024 or d == 0
