@@ -69,7 +69,8 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (1, 11, 2), (4, 9, 1), (2, 9, 1), (3, 8, 1), (3, 8, 3)]  # (B, d, head_select)
+# (B, d, head_select[, deep_levels]); without deep_levels the library's default (three levels here)
+HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (1, 11, 2), (4, 9, 1), (2, 9, 1), (3, 8, 1), (3, 8, 3), (3, 9, 2, 2)]
 HBM_LAUNCHES = [(768, 32, 8, 2), (768, 32, 16, 2), (1024, 32, 16, 2), (768, 32, 16, 3)]  # tile, warps, refill, buffers
 # the value workloads: the regression forest's trees resemble the hbm ones; the
 # boosted trees (depth <= 6) fit whole in a level head of depth 5
@@ -105,6 +106,7 @@ def parse():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--bin-buffers", type=int, default=0)
+    ap.add_argument("--deep-levels", type=int, default=0, help="tree levels per super-node: 2, 3 (0: default)")
     ap.add_argument("--pass-bytes", type=int, default=0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
@@ -296,7 +298,7 @@ def tuned_forest(args, forest, X, name):
     tuning = None
     if explicit or args.no_autotune:
         params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes,
-                      head_select=args.head_select)
+                      head_select=args.head_select, deep_levels=args.deep_levels)
         df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
         df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill,
                      bin_buffers=args.bin_buffers)
@@ -439,8 +441,8 @@ def run_packed(args, ws, rank, local):
     avg_launch_ms = statistics.mean(per_launch_ms)
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "obs_tile", "warps_per_cta",
-                                   "refill_lanes", "bin_buffers")}
+    params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "obs_tile",
+                                   "warps_per_cta", "refill_lanes", "bin_buffers")}
     traffic = profiled_traffic(name, params, n)
     kernel = "fp_traverse_kernel<values>" if values else "fp_traverse_kernel<votes>"
     visits_per_s = visits_per_obs * n / (avg_launch_ms / 1e3)
@@ -652,14 +654,23 @@ def run_ablation(args, ws, rank, local):
     no_stats.cardinality = None  # packed without statistics: children keep left-first order
     best = at.autotune(forest, X[: min(n, 1 << 20)], layouts=HBM_LAYOUTS if name == "hbm" else None,
                        launches=HBM_LAUNCHES if name == "hbm" else None)
+    # the paper's layouts with two-level super-nodes (full thresholds), then
+    # the same with three-level ones, then the autotuner's choice
     variants = [
-        ("DF order, roots only (no statistics)", no_stats, dict(bin_size=1, interleave_depth=0), {}),
-        ("Stat (training cardinalities), roots only", forest, dict(bin_size=1, interleave_depth=0), {}),
-        ("Stat (counted on 200k observations), roots only", inferred, dict(bin_size=1, interleave_depth=0), {}),
-        ("Bin B=16, levels 0..4", forest, dict(bin_size=16, interleave_depth=4, head_select=1), {}),
-        ("Bin B=16, 31 most visited nodes", forest, dict(bin_size=16, interleave_depth=4, head_select=3), {}),
-        ("Bin B=3, levels 0..8", forest, dict(bin_size=3, interleave_depth=8, head_select=1), {}),
-        ("Bin B=3, 511 most visited nodes", forest, dict(bin_size=3, interleave_depth=8, head_select=3), {}),
+        ("DF order, roots only (no statistics)", no_stats, dict(bin_size=1, interleave_depth=0, deep_levels=2), {}),
+        ("Stat (training cardinalities), roots only", forest, dict(bin_size=1, interleave_depth=0, deep_levels=2), {}),
+        ("Stat (counted on 200k observations), roots only", inferred,
+         dict(bin_size=1, interleave_depth=0, deep_levels=2), {}),
+        ("Bin B=16, levels 0..4", forest, dict(bin_size=16, interleave_depth=4, head_select=1, deep_levels=2), {}),
+        ("Bin B=16, 31 most visited nodes", forest,
+         dict(bin_size=16, interleave_depth=4, head_select=3, deep_levels=2), {}),
+        ("Bin B=3, levels 0..8", forest, dict(bin_size=3, interleave_depth=8, head_select=1, deep_levels=2), {}),
+        ("Bin B=3, 511 most visited nodes", forest,
+         dict(bin_size=3, interleave_depth=8, head_select=3, deep_levels=2), {}),
+        ("Stat, roots only, three-level super-nodes", forest, dict(bin_size=1, interleave_depth=0, deep_levels=3),
+         {}),
+        ("Bin B=3, levels 0..8, three-level super-nodes", forest,
+         dict(bin_size=3, interleave_depth=8, head_select=1, deep_levels=3), {}),
         ("autotuned", forest, {k: best[k] for k in at.LAYOUT_KEYS}, {k: best[k] for k in at.LAUNCH_KEYS}),
     ]
     for label, f, params, launch in variants:

@@ -107,7 +107,13 @@ typedef struct fp_forest_desc {
  *                     0 = default: 2 when d is odd, else 1
  *   bin_buffers       shared-memory buffers that bin blocks stream through,
  *                     2 or 3 (0 = 3): two leave room for larger heads or
- *                     tiles, three hide copy latency better */
+ *                     tiles, three hide copy latency better
+ *   deep_levels       tree levels per 32-byte super-node below the head: 2
+ *                     (full thresholds), 3 (thresholds shortened to key
+ *                     prefixes, ties decided by a side table of full keys;
+ *                     needs ceil(log2 F) + 2 * ceil(log2 C) <= 24, classes
+ *                     not counted for forests with leaf values), or
+ *                     0 = default: 3 when that sum is at most 12, else 2 */
 typedef struct fp_pack_params {
     int32_t bin_size;
     int32_t interleave_depth;
@@ -117,7 +123,7 @@ typedef struct fp_pack_params {
     int32_t refill_lanes;
     int32_t head_select;
     int32_t bin_buffers;
-    int32_t reserved;         /* must be 0 */
+    int32_t deep_levels;
 } fp_pack_params;
 
 typedef struct fp_packed_forest fp_packed_forest; /* host image, opaque */
@@ -140,6 +146,7 @@ typedef struct fp_packed_info {
     int32_t head_nodes;       /* 2^(d+1)-1: head nodes per tree at most */
     int32_t head_select;
     int32_t bin_buffers;
+    int32_t deep_levels;      /* tree levels per super-node (2 or 3) */
 } fp_packed_info;
 
 /* Build the packed host image of a forest (Section III-A: DF-, Stat, Bin).

@@ -20,8 +20,8 @@ import numpy as np
 from . import FPError, fp_pack_forest, fp_predict, fp_predict_values, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
-LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select")
-_SEARCH_VERSION = "heads-v6"  # cached results of an older search space are not reused
+LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select", "deep_levels")
+_SEARCH_VERSION = "deep3-v7"  # cached results of an older search space are not reused
 LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")
 
 
@@ -36,12 +36,14 @@ def block_bytes(bin_size: int, depth: int, head_select: int = 1) -> int:
 
 
 def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int | None = None
-                      ) -> list[tuple[int, int, int]]:
-    """(B, d, head_select) triples to try: for bins of 1, 3, 8, 16 and 64
-    trees, the deepest paired level head (head_select 2, d odd) and the
-    deepest level head (head_select 1) whose block fits the limit, and a
+                      ) -> list[tuple[int, ...]]:
+    """(B, d, head_select[, deep_levels]) tuples to try: for bins of 1, 3, 8,
+    16 and 64 trees, the deepest paired level head (head_select 2, d odd) and
+    the deepest level head (head_select 1) whose block fits the limit, and a
     small paired head (d = 3), which leaves shared memory to tiles of wide
-    rows or to a second CTA per SM; and one ranked head (head_select 3)."""
+    rows or to a second CTA per SM; one ranked head (head_select 3); all with
+    the library's default super-nodes, and the first paired head of bins of
+    3 again with two-level super-nodes."""
     out = []
 
     def add(c):
@@ -57,6 +59,9 @@ def candidate_layouts(n_trees: int, limit: int = _BLOCK_LIMIT, max_layouts: int 
         add((B, 3, 2))
     B = min(3, n_trees)
     add((B, min(9, max(d for d in range(10) if block_bytes(B, d, 3) <= limit or d == 0)), 3))
+    first3 = [c for c in out if c[0] == B and c[2] == 2]
+    if first3:
+        add(first3[0] + (2,))
     if max_layouts is not None and len(out) > max_layouts:
         idx = np.linspace(0, len(out) - 1, max_layouts).round().astype(int)
         out = [out[i] for i in sorted(set(idx))]
@@ -143,12 +148,14 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
     for lay in layouts:
         B, d = lay[0], lay[1]
         sel = lay[2] if len(lay) > 2 else 0  # 0: the library's default head kind
+        dl = lay[3] if len(lay) > 3 else 0   # 0: the library's default super-nodes
         t0 = time.perf_counter()
         try:
-            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel))
+            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl))
         except FPError as e:
-            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, error=str(e)))
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, error=str(e)))
             continue
+        dl = df.info["deep_levels"]
         pack_s = time.perf_counter() - t0
         for launch in (launches or candidate_launches(df.info["obs_tile"])):
             tile, warps, refill = launch[:3]
@@ -156,14 +163,14 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
             try:
                 df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
             except FPError as e:
-                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=tile,
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, obs_tile=tile,
                                   warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf, error=str(e)))
                 continue
             ms = _time_predict(df, X, cls, reps)
             if ref is None:
                 ref = cls.clone()
             same = _same(ref, cls)
-            row = dict(bin_size=B, interleave_depth=d, head_select=sel, obs_tile=df.info["obs_tile"],
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, obs_tile=df.info["obs_tile"],
                        warps_per_cta=warps, bin_buffers=nbuf,
                        refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)
             table.append(row)

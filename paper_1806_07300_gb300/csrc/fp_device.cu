@@ -202,6 +202,17 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.status = f->d_status;
     p.spin_limit = f->spin_limit;
     p.stall = f->stall;
+    p.n_super = h.n_super;
+    p.deep3 = h.deep_levels == 3;
+    if (p.deep3) {
+        p.fbits = (uint32_t)h.feature_bits;
+        p.cbits = (uint32_t)h.class_bits;
+        p.sh2 = p.fbits + 2 * p.cbits;
+        p.fmask = (1u << p.fbits) - 1u;
+        p.cmask = (1u << p.cbits) - 1u;
+        p.vbase3 = (uint32_t)h.values3_base;
+        p.deep_keys = reinterpret_cast<const uint32_t *>(f->d_image + h.off_deep_keys);
+    }
     return p;
 }
 

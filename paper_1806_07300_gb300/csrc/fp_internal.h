@@ -15,10 +15,22 @@
 //                                    exit[e*stride + k]   = e-th exit of tree k
 //   deep     FpSuper[]           per tree, its super-nodes in Stat order; the
 //                                trees' regions follow one another
+//   deep_keys uint32[8] per super-node (three-level super-nodes only): the
+//                                full keys of its seven nodes (slot 7 zero)
+//   values   float[n_values]     forests with leaf values (see below)
 //   --- end of the classification part (class_bytes) ---
 //   parity blocks                per bin, int32 leaf id of each exit (or -1),
 //                                [nexits][stride] like the exits
-//   deep_leaf int32[4] per super-node: leaf id behind each exit, or -1
+//   deep_leaf int32[4] (two-level) or [8] (three-level) per super-node: leaf
+//                                id behind each exit, or -1
+//
+// Thresholds are stored as order keys, not floats.  key(v) maps a float to a
+// uint32 that orders like the float: +0 for -0, then the sign bit flipped for
+// v >= 0 and every bit flipped for v < 0; a NaN observation value maps to
+// 0xFFFFFFFF and a NaN threshold to 0.  For every observation value x and
+// threshold t, x <= t (go left) exactly when key(x) <= key(t) -- a NaN x or t
+// goes right, as the float compare does -- so the kernel converts the rows
+// once when it stages them and every compare is an unsigned integer compare.
 //
 // Three kinds of head (the header's head_select, the same for every bin; 1
 // and 2 are the level heads, 3 the ranked one):
@@ -57,24 +69,47 @@
 //               its slot in values[] (forests with leaf values)
 //   bit 31 = 0: a super-node, the index into deep[] (so fewer than 2^31)
 //
-// Forests with leaf values also hold values[n_values] (float, one slot per
-// leaf, numbered tree by tree in node order) at off_values, inside the
-// classification part of the image.
+// Forests with leaf values also hold values[n_values] (float) at off_values,
+// inside the classification part of the image: one slot per leaf, numbered
+// tree by tree in node order, and with three-level super-nodes, from
+// values3_base on, eight more per super-node (the value behind each exit).
 //
-// Super-node (32 bytes, one L2 sector, 32-byte aligned): a node v below the
-// head together with its two children, i.e. two levels of the tree resolved
-// by one load:
-//   w[0] threshold of v            w[1] threshold of v's left child
-//   w[2] threshold of v's right child
+// Super-nodes come in two kinds (the header's deep_levels), 32 bytes each
+// (one L2 sector, 32-byte aligned, one load):
+//
+// deep_levels = 2: a node v below the head together with its two children,
+// i.e. two levels of the tree resolved by one load:
+//   w[0] key of v's threshold      w[1] key of v's left child's threshold
+//   w[2] key of v's right child's threshold
 //   w[3] features: v [9:0], left child [19:10], right child [29:20]
 //   w[4..7] exits: (left,left) (left,right) (right,left) (right,right)
 // A child that is a leaf keeps a dummy split and both of its exits name the
 // leaf, so either outcome of the dummy compare lands on it.
+//
+// deep_levels = 3: a node v and the two levels below it -- seven nodes in
+// implicit slots (slot i has children 2i+1, 2i+2; a leaf is carried down as
+// dummies, like the level heads) and eight exits (exit e is child e & 1 of
+// slot 3 + (e >> 1)) -- three levels per load.  With fb = feature_bits and
+// cb = class_bits:
+//   w[0..2] slots 0..2: [31:fb] the top 32-fb bits of the key, [fb-1:0] feature
+//   w[3..6] slots 3..6: [31:fb+2cb] the top 32-fb-2cb bits of the key,
+//           [fb+2cb-1:fb+cb] class of the right exit, [fb+cb-1:fb] class of
+//           the left exit (a leaf exit's class; 0 otherwise), [fb-1:0] feature
+//   w[7]    [31:24] leaf mask (bit e set: exit e is a leaf),
+//           [23:0]  offset from this super-node to the first of its children:
+//           the super-nodes rooted at its internal exits are consecutive, in
+//           exit order, so exit e continues at this + offset + (number of
+//           internal exits before e)
+// The walk compares the key of x with a key prefix; when the prefixes are
+// equal it decides with the full key from deep_keys (one more load, for a
+// small fraction of compares).  A dummy slot has key 0 (never a tie).  In a
+// forest with leaf values exit e of super-node g names the value slot
+// values3_base + 8g + e.
 #pragma once
 #include <stdint.h>
 
 #define FP_IMAGE_MAGIC 0x4B435046u /* "FPCK" */
-#define FP_IMAGE_VERSION 5u
+#define FP_IMAGE_VERSION 6u
 
 #define FP_MAX_FEATURES 1024
 #define FP_MAX_CLASSES 512
@@ -83,6 +118,7 @@
 #define FP_MAX_LEVEL_DEPTH 11  // level heads
 #define FP_TARGET_BITS 11
 #define FP_TARGET_MASK 2047u
+#define FP_DEEP3_OFFSET_MASK 0xFFFFFFu  // three-level super-nodes: child offset field
 
 struct FpSuper {
     uint32_t w[8];
@@ -121,4 +157,9 @@ struct FpImageHeader {
     int64_t head_bytes_total, pass_bytes;
     int64_t n_internal;            // internal nodes of the forest
     int64_t n_values, off_values;  // leaf-value slots (0 for a classification forest)
+    int32_t deep_levels;           // 2 or 3 tree levels per super-node
+    int32_t feature_bits, class_bits;  // three-level super-nodes: field widths fb, cb
+    int32_t reserved0;
+    int64_t off_deep_keys;         // three-level super-nodes: full keys, 8 per super-node
+    int64_t values3_base;          // forests with leaf values: first slot of the per-exit values
 };

@@ -16,11 +16,14 @@
 //        leaf carries its class (the paper's shared per-class nodes, folded
 //        into the reference so no load is spent on them);
 //   Stat (Section III-A): below the interleaved levels a tree is cut into
-//        super-nodes of two levels (a node and its two children: one 32-byte
-//        sector, one load) laid out depth-first with the child super-node of
-//        largest training cardinality immediately after its parent -- the
-//        paper's "more likely path adjacent" rule at the granularity of the
-//        GPU's memory transaction.
+//        super-nodes (one 32-byte sector, one load) of two levels (a node
+//        and its two children) laid out depth-first with the child
+//        super-node of largest training cardinality immediately after its
+//        parent -- the paper's "more likely path adjacent" rule at the
+//        granularity of the GPU's memory transaction -- or of three levels
+//        (seven nodes, thresholds shortened to key prefixes), whose children
+//        sit side by side and whose most frequently reached child is laid
+//        out first.
 // The image format is described in fp_internal.h.
 #include <algorithm>
 #include <cstdio>
@@ -57,6 +60,24 @@ struct fp_packed_forest {
 namespace {
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// The order key of a threshold: x <= t exactly when key(x) <= thr_key(t),
+// with the kernel's key of an observation value (NaN -> 0xFFFFFFFF); a NaN
+// threshold gets 0, below every observation key, so every x goes right.
+uint32_t thr_key(float t) {
+    uint32_t u;
+    memcpy(&u, &t, 4);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return 0u;
+    if (u == 0x80000000u) u = 0u;  // -0 orders as +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// bits that hold the values 0 .. n-1 (at least 1)
+int32_t bits_for(int32_t n) {
+    int32_t b = 1;
+    while (b < 31 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
 
 struct TreeRef {
     const int32_t *L, *R, *Fe, *Cl;
@@ -124,6 +145,7 @@ struct TreeLayout {
     std::vector<int32_t> exits;      // node id behind each exit (leaf or deep root)
     std::vector<int32_t> sn_root;    // root node of each super-node, in layout order
     std::vector<int32_t> sn_index;   // node id -> super-node index (-1 if it roots none)
+    std::vector<int32_t> sn_first;   // three-level: super-node index -> its first child's index (0: none)
     std::vector<int32_t> leaf_rank;  // forests with leaf values: node id -> rank among the tree's leaves
     int64_t value_base = -1;         // forests with leaf values: the tree's first value slot
 };
@@ -136,9 +158,26 @@ void super_exits(const TreeRef &t, int32_t v, int32_t e[4]) {
     if (t.leaf(r)) { e[2] = e[3] = r; } else { e[2] = t.L[r]; e[3] = t.R[r]; }
 }
 
+// The seven slots and eight exits of the three-level super-node rooted at v;
+// a leaf is carried down into every slot and exit below it.
+void slots3(const TreeRef &t, int32_t v, int32_t s[7], int32_t e[8]) {
+    s[0] = v;
+    for (int i = 0; i < 7; ++i) {
+        const int32_t u = s[i];
+        const int32_t l = t.leaf(u) ? u : t.L[u], r = t.leaf(u) ? u : t.R[u];
+        if (i < 3) {
+            s[2 * i + 1] = l;
+            s[2 * i + 2] = r;
+        } else {
+            e[2 * (i - 3)] = l;
+            e[2 * (i - 3) + 1] = r;
+        }
+    }
+}
+
 int64_t card_of(const TreeRef &t, int32_t v) { return t.Card ? t.Card[v] : 0; }
 
-int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti);
+int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti, bool three);
 
 // Head, when select_levels is set: levels 0..d in K = 2^(d+1)-1 implicit
 // breadth-first slots (the interleaved levels of the Bin layout).
@@ -150,7 +189,8 @@ int finish_super(const TreeRef &t, struct TreeLayout &out, int32_t ti);
 // the tree is cut into super-nodes (a node and its two children: one 32-byte
 // sector, one load) laid out depth-first with the child super-node of largest
 // cardinality right after its parent (Stat at super-node granularity).
-int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, TreeLayout &out, int32_t ti) {
+int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, bool three, TreeLayout &out,
+                int32_t ti) {
     const int32_t m = (int32_t)t.m;
     if (select_levels) {
         // implicit breadth-first slots of levels 0..d; a leaf above level d+1
@@ -169,7 +209,7 @@ int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, Tree
             }
         }
         out.head.clear();
-        return finish_super(t, out, ti);
+        return finish_super(t, out, ti, three);
     }
     std::vector<int32_t> depth((size_t)m, 0);
     std::vector<int32_t> order;  // breadth-first
@@ -216,7 +256,7 @@ int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, Tree
         out.head.push_back(0);
         out.exits.push_back(0);
         out.head_meta.push_back(0);  // targets are fixed up once the bin's nranks is known
-        return finish_super(t, out, ti);
+        return finish_super(t, out, ti, three);
     }
     std::vector<int32_t> rank((size_t)m, -1);
     std::vector<int32_t> stack{0};
@@ -243,16 +283,54 @@ int layout_tree(const TreeRef &t, int32_t K, int32_t d, bool select_levels, Tree
         return FP_EUNSUPPORTED;
     }
     out.rank = rank;
-    return finish_super(t, out, ti);
+    return finish_super(t, out, ti, three);
 }
 
-// Super-nodes below the head, rooted at the internal exits: depth-first,
-// the child super-node of largest cardinality right after its parent.
-int finish_super(const TreeRef &t, TreeLayout &out, int32_t ti) {
+// Super-nodes below the head, rooted at the internal exits.  Two levels:
+// depth-first, the child super-node of largest cardinality right after its
+// parent.  Three levels: a super-node's children get consecutive indices in
+// exit order (so one offset locates them all), and the children are expanded
+// depth-first, most frequently reached first.
+int finish_super(const TreeRef &t, TreeLayout &out, int32_t ti, bool three) {
     const int32_t m = (int32_t)t.m;
     out.sn_index.assign((size_t)m, -1);
     out.sn_root.clear();
+    out.sn_first.clear();
     std::vector<int32_t> stack;
+    if (three) {
+        for (int32_t root : out.exits) {
+            if (t.leaf(root) || out.sn_index[root] >= 0) continue;
+            out.sn_index[root] = (int32_t)out.sn_root.size();
+            out.sn_root.push_back(root);
+            out.sn_first.push_back(0);
+            stack.push_back(root);
+            while (!stack.empty()) {
+                const int32_t v = stack.back();
+                stack.pop_back();
+                int32_t sl[7], e[8], kids[8];
+                slots3(t, v, sl, e);
+                int nk = 0;
+                for (int q = 0; q < 8; ++q)
+                    if (!t.leaf(e[q])) kids[nk++] = e[q];
+                if (nk == 0) continue;
+                const int64_t first = (int64_t)out.sn_root.size();
+                if (first - out.sn_index[v] > (int64_t)FP_DEEP3_OFFSET_MASK || first + nk >= (int64_t)INT32_MAX) {
+                    fp_set_error("tree %d: three-level super-node offsets exceed 24 bits; use deep_levels = 2", ti);
+                    return FP_EUNSUPPORTED;
+                }
+                out.sn_first[out.sn_index[v]] = (int32_t)first;
+                for (int q = 0; q < nk; ++q) {
+                    out.sn_index[kids[q]] = (int32_t)out.sn_root.size();
+                    out.sn_root.push_back(kids[q]);
+                    out.sn_first.push_back(0);
+                }
+                if (t.Card)
+                    std::stable_sort(kids, kids + nk, [&](int32_t a, int32_t b) { return t.Card[a] > t.Card[b]; });
+                for (int q = nk - 1; q >= 0; --q) stack.push_back(kids[q]);
+            }
+        }
+        return FP_OK;
+    }
     for (int32_t root : out.exits) {
         if (t.leaf(root) || out.sn_index[root] >= 0) continue;
         stack.push_back(root);
@@ -291,10 +369,9 @@ uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base
 void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base, FpSuper &sn,
                   int32_t leaf_ids[4]) {
     const int32_t l = t.L[v], r = t.R[v];
-    float th0 = t.Th[v], th1 = t.leaf(l) ? 0.0f : t.Th[l], th2 = t.leaf(r) ? 0.0f : t.Th[r];
-    memcpy(&sn.w[0], &th0, 4);
-    memcpy(&sn.w[1], &th1, 4);
-    memcpy(&sn.w[2], &th2, 4);
+    sn.w[0] = thr_key(t.Th[v]);
+    sn.w[1] = t.leaf(l) ? 0u : thr_key(t.Th[l]);
+    sn.w[2] = t.leaf(r) ? 0u : thr_key(t.Th[r]);
     const uint32_t fl = t.leaf(l) ? 0u : (uint32_t)t.Fe[l], fr = t.leaf(r) ? 0u : (uint32_t)t.Fe[r];
     sn.w[3] = (uint32_t)t.Fe[v] | (fl << 10) | (fr << 20);
     int32_t e[4];
@@ -303,6 +380,37 @@ void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t ba
         sn.w[4 + q] = ref_of(t, lay, e[q], base);
         leaf_ids[q] = t.leaf(e[q]) ? e[q] : -1;
     }
+}
+
+// A three-level super-node (format in fp_internal.h): key prefixes and
+// features of its seven slots, leaf classes in the last level's words, the
+// leaf mask and the offset to its first child; the full keys, the leaf ids
+// and (forests with leaf values) the exits' values go to side tables.
+void encode_super3(const TreeRef &t, const TreeLayout &lay, int32_t v, int32_t fb, int32_t cb, const float *leaf_value,
+                   FpSuper &sn, uint32_t keys[8], int32_t leaf_ids[8], float *vals) {
+    int32_t sl[7], e[8];
+    slots3(t, v, sl, e);
+    for (int i = 0; i < 7; ++i) {
+        const int32_t u = sl[i];
+        const uint32_t key = t.leaf(u) ? 0u : thr_key(t.Th[u]);
+        const int32_t sh = i < 3 ? fb : fb + 2 * cb;
+        keys[i] = key;
+        sn.w[i] = (key & ~((1u << sh) - 1u)) | (t.leaf(u) ? 0u : (uint32_t)t.Fe[u]);
+    }
+    keys[7] = 0;
+    uint32_t mask = 0;
+    for (int q = 0; q < 8; ++q) {
+        const int32_t c = e[q];
+        leaf_ids[q] = -1;
+        if (vals) vals[q] = 0.0f;
+        if (!t.leaf(c)) continue;
+        mask |= 1u << q;
+        leaf_ids[q] = c;
+        if (cb) sn.w[3 + q / 2] |= (uint32_t)t.Cl[c] << (fb + cb * (q & 1));
+        if (vals) vals[q] = leaf_value[c];
+    }
+    const int32_t first = lay.sn_first[lay.sn_index[v]];
+    sn.w[7] = (mask << 24) | (first ? (uint32_t)(first - lay.sn_index[v]) : 0u);
 }
 
 }  // namespace
@@ -337,6 +445,9 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
     const bool select_levels = kind == 1 || kind == 2;  // level heads: single or paired slots
     const bool paired = kind == 2;
+    // three-level super-nodes: feature and class fields beside the key prefixes
+    const int32_t fb = bits_for(F), cb = desc->leaf_value ? 0 : (C > 1 ? bits_for(C) : 0);
+    const bool three = p.deep_levels == 3 || (p.deep_levels == 0 && fb + 2 * cb <= 12);
     int32_t R = p.obs_tile;
     if (R == 0) {  // rows take up to ~96 KiB of shared memory
         int64_t r = (96 * 1024) / ((int64_t)F * 4);
@@ -347,11 +458,17 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     if (B < 1 || B > 1024 || d < 0 || d > (select_levels ? FP_MAX_LEVEL_DEPTH : FP_MAX_DEPTH) || W < 1 || W > 32 ||
         R < 32 || R > 2048 || R % 32 ||
         refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 3 || (paired && d % 2 == 0) ||
-        (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) || p.reserved != 0) {
+        (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) ||
+        (p.deep_levels != 0 && p.deep_levels != 2 && p.deep_levels != 3)) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
-                     "refill %d, head_select %d, bin_buffers %d)", B, d, R, W, refill, p.head_select,
-                     p.bin_buffers);
+                     "refill %d, head_select %d, bin_buffers %d, deep_levels %d)", B, d, R, W, refill,
+                     p.head_select, p.bin_buffers, p.deep_levels);
         return FP_EINVAL;
+    }
+    if (three && fb + 2 * cb > 24) {
+        fp_set_error("fp_pack_forest: %d features and %d classes leave three-level super-nodes too few key bits; "
+                     "use deep_levels = 2", F, C);
+        return FP_EUNSUPPORTED;
     }
     if (B > T) B = T;
     const int32_t K = (1 << (d + 1)) - 1;
@@ -373,7 +490,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                        desc->cardinality ? desc->cardinality + b : nullptr, e - b};
             int rc = validate_tree(tr, F, C, t, seen);
             if (rc) return rc;
-            rc = layout_tree(tr, K, d, select_levels, lays[t], t);
+            rc = layout_tree(tr, K, d, select_levels, three, lays[t], t);
             if (rc) return rc;
             deep_count[t] = (int64_t)lays[t].sn_root.size();
             for (int64_t v = 0; v < tr.m; ++v) n_internal += !tr.leaf((int32_t)v);
@@ -448,9 +565,18 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         std::vector<int64_t> tree_base((size_t)T + 1, 0);
         for (int32_t t = 0; t < T; ++t) tree_base[t + 1] = tree_base[t] + deep_count[t];
         const int64_t n_deep = tree_base[T];
-        if (n_deep >= (int64_t)FP_REF_LEAF) {
+        if (n_deep >= (int64_t)FP_REF_LEAF || (three && 8 * n_deep >= (int64_t)FP_REF_LEAF)) {
             fp_set_error("fp_pack_forest: %lld super-nodes exceed the 31-bit references", (long long)n_deep);
             return FP_EUNSUPPORTED;
+        }
+        // three-level super-nodes of a forest with leaf values: eight value slots each
+        const int64_t values3_base = n_values;
+        if (desc->leaf_value && three) {
+            n_values += 8 * n_deep;
+            if (n_values >= (int64_t)FP_REF_LEAF) {
+                fp_set_error("fp_pack_forest: more than 2^31 leaf-value slots; use deep_levels = 2");
+                return FP_EUNSUPPORTED;
+            }
         }
         // passes: consecutive bins whose records fit the budget
         std::vector<FpPass> passes;
@@ -482,11 +608,16 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.off_tree_base = off; off = align_up(off + 4 * (int64_t)T, 256);
         h.off_heads = off; off = align_up(off + head_total, 256);
         h.off_deep = off; off = align_up(off + (int64_t)sizeof(FpSuper) * n_deep, 256);
+        h.deep_levels = three ? 3 : 2;
+        h.feature_bits = three ? fb : 0;
+        h.class_bits = three ? cb : 0;
+        h.off_deep_keys = off; off = align_up(off + (three ? 32 * n_deep : 0), 256);
         h.n_values = n_values;
+        h.values3_base = values3_base;
         h.off_values = off; off = align_up(off + 4 * n_values, 256);
         h.class_bytes = off;
         h.off_pheads = off; off = align_up(off + phead_total, 256);
-        h.off_deep_leaf = off; off = align_up(off + 16 * n_deep, 256);
+        h.off_deep_leaf = off; off = align_up(off + (three ? 32 : 16) * n_deep, 256);
         h.total_bytes = off;
 
         auto *pf = new fp_packed_forest;
@@ -528,7 +659,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                             uint32_t w[4] = {0, 0, 0, 0};
                             for (int c = 0; c < 3; ++c) {
                                 if (tr.leaf(vv[c])) continue;  // dummy: any outcome lands on the same leaf
-                                memcpy(&w[c], &tr.Th[vv[c]], 4);
+                                w[c] = thr_key(tr.Th[vv[c]]);
                                 w[3] |= (uint32_t)tr.Fe[vv[c]] << (10 * c);
                             }
                             memcpy(blk + (q * bn.stride + k) * 16, w, 16);
@@ -544,7 +675,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 if (select_levels) {
                     for (size_t s = 0; s < lay.slot.size(); ++s) {
                         const int32_t v = lay.slot[s];
-                        const float thr = tr.leaf(v) ? 0.0f : tr.Th[v];
+                        const uint32_t thr = tr.leaf(v) ? 0u : thr_key(tr.Th[v]);
                         const uint32_t meta = tr.leaf(v) ? 0u : (uint32_t)tr.Fe[v] << 22;
                         uint8_t *rec = blk + ((int64_t)s * bn.stride + k) * 8;
                         memcpy(rec, &thr, 4);
@@ -561,13 +692,13 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 size_t next_exit = 0;
                 for (size_t i = 0; i < lay.head.size(); ++i) {
                     const int32_t v = lay.head[i];
-                    float thr = 0.0f;
+                    uint32_t thr = 0u;
                     uint32_t meta, tgt[2];
                     if (tr.leaf(v)) {  // single-leaf tree
                         tgt[0] = tgt[1] = (uint32_t)bn.nranks;
                         meta = 0;
                     } else {
-                        thr = tr.Th[v];
+                        thr = thr_key(tr.Th[v]);
                         meta = (uint32_t)tr.Fe[v] << 22;
                         const int32_t c2[2] = {tr.L[v], tr.R[v]};
                         for (int s2 = 0; s2 < 2; ++s2) {
@@ -611,7 +742,16 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             const TreeLayout &lay = lays[t];
             for (size_t i = 0; i < lay.sn_root.size(); ++i) {
                 const int64_t g = tree_base[t] + (int64_t)i;
-                encode_super(tr, lay, lay.sn_root[i], tree_base[t], deep[g], dleaf + 4 * g);
+                if (three) {
+                    uint32_t *keys = reinterpret_cast<uint32_t *>(img + h.off_deep_keys) + 8 * g;
+                    float *vals = desc->leaf_value
+                                      ? reinterpret_cast<float *>(img + h.off_values) + values3_base + 8 * g
+                                      : nullptr;
+                    encode_super3(tr, lay, lay.sn_root[i], fb, cb, desc->leaf_value ? desc->leaf_value + nb : nullptr,
+                                  deep[g], keys, dleaf + 8 * g, vals);
+                } else {
+                    encode_super(tr, lay, lay.sn_root[i], tree_base[t], deep[g], dleaf + 4 * g);
+                }
             }
         }
         *out = pf;
@@ -656,6 +796,7 @@ void fp_fill_info(const FpImageHeader *h, fp_packed_info *info) {
     info->passes = h->n_passes;
     info->refill_lanes = h->refill_lanes;
     info->bin_buffers = h->bin_buffers;
+    info->deep_levels = h->deep_levels;
 }
 
 extern "C" const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes) {

@@ -8,7 +8,9 @@
 //   1. stages the tile's rows into shared memory feature-major
 //      (x[f * R + r]), so 32 lanes holding 32 consecutive rows read any
 //      features from 32 different banks (16-byte loads along a row when the
-//      feature count is a multiple of 4, else 4-byte cp.async);
+//      feature count is a multiple of 4, else 4-byte cp.async), each value
+//      turned into its order key (fp_internal.h), so every compare below is
+//      an unsigned integer compare;
 //   2. streams the bins' interleaved blocks (the heads of their trees,
 //      Section III-A Bin) through nbuf (2 or 3) shared-memory buffers with TMA bulk
 //      copies (cp.async.bulk) completing on mbarriers: a warp waits only for
@@ -23,9 +25,10 @@
 //                 heads: until the last lane leaves the head); paths that leave the
 //                 head are pushed, compacted with __ballot_sync / __popc,
 //                 into the warp's ring of pending tasks;
-//        deep  -- every lane holding a task resolves two more levels with one
-//                 32-byte super-node load (one L2 sector); a lane that reaches
-//                 a leaf votes and takes the next pending task from the ring.
+//        deep  -- every lane holding a task resolves two or three more levels
+//                 with one 32-byte super-node load (one L2 sector); a lane
+//                 that reaches a leaf votes and takes the next pending task
+//                 from the ring.
 //      Bursts keep the ring topped up, so lanes stay busy while paths of very
 //      different depth diverge -- the GPU form of the paper's round-robin over
 //      independent tasks (Section III-B).  Pending and running tasks carry
@@ -86,6 +89,12 @@ struct TravParams {
     float *acc_val;           // values mode, several passes: per-row accumulator
     int32_t spin_limit;       // polls of a bin block's barrier before the wait gives up
     int32_t stall;            // fault injection: bin waits ignore completed copies (0 normally)
+    int32_t deep3;            // super-nodes of three levels (else two)
+    uint32_t fbits, sh2;      // three levels: feature bits; key-prefix shift of the last level
+    uint32_t cbits, fmask, cmask;  // three levels: class bits, feature and class masks
+    uint32_t vbase3;          // three levels, values mode: first per-exit value slot
+    const uint32_t *deep_keys;  // three levels: full keys, 8 per super-node
+    int64_t n_super;
 };
 
 // What a kernel computes per (row, tree) task it finishes.
@@ -128,6 +137,15 @@ __device__ __forceinline__ void ld_super(const FpSuper *p, uint32_t w[8]) {
 }
 
 __device__ __forceinline__ void report(int32_t *status, int32_t code) { atomicCAS(status, 0, code); }
+
+// The order key of an observation value (fp_internal.h): compares like the
+// float against threshold keys; NaN goes above every threshold (right).
+__device__ __forceinline__ uint32_t obs_key(float v) {
+    uint32_t u = __float_as_uint(v);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return 0xFFFFFFFFu;
+    if (u == 0x80000000u) u = 0u;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -205,30 +223,84 @@ __device__ __forceinline__ void pop_tasks(const TravParams &p, const uint2 *ring
     head += npop;
 }
 
-// One deep step, two levels of the tree per 32-byte load, in two halves: the
-// load is issued first and consumed after the warp has done other work (a
-// head burst), so the L2 latency overlaps that work.
+// One deep step, two or three levels of the tree per 32-byte load, in two
+// halves: the load is issued first and consumed after the warp has done other
+// work (a head burst), so the L2 latency overlaps that work.
 __device__ __forceinline__ void deep_issue(const TravParams &p, const LaneTask &L, uint32_t w[8]) {
     ld_super(p.deep + L.ref, w);
 }
 
+// Three levels: the key of x against each slot's key prefix; a tie of the
+// prefixes (rare) is decided again from the full keys of the super-node.
 template <int MODE>
-__device__ __forceinline__ void deep_finish(const TravParams &p, const float *xs, uint32_t *svotes, int64_t row0,
-                                            LaneTask &L, const uint32_t w[8]) {
+__device__ __forceinline__ void deep_finish3(const TravParams &p, const uint32_t *xs, uint32_t *svotes, int64_t row0,
+                                             LaneTask &L, const uint32_t w[8]) {
+    const uint32_t *xr = xs + L.r;
     const int R = p.R;
-    const float x0 = xs[(w[3] & 1023u) * R + L.r];
-    const uint32_t d0 = x0 <= __uint_as_float(w[0]) ? 0u : 1u;
+    const uint32_t fm = p.fmask, s1 = p.fbits, s2 = p.sh2;
+    const uint32_t k0 = xr[(w[0] & fm) * R];
+    uint32_t d0 = (k0 >> s1) > (w[0] >> s1) ? 1u : 0u;
+    bool tie = (k0 >> s1) == (w[0] >> s1);
+    uint32_t n1 = d0 ? w[2] : w[1];
+    uint32_t k1 = xr[(n1 & fm) * R];
+    uint32_t d1 = (k1 >> s1) > (n1 >> s1) ? 1u : 0u;
+    tie |= (k1 >> s1) == (n1 >> s1);
+    uint32_t n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
+    uint32_t k2 = xr[(n2 & fm) * R];
+    uint32_t d2 = (k2 >> s2) > (n2 >> s2) ? 1u : 0u;
+    tie |= (k2 >> s2) == (n2 >> s2);
+    if (tie) {
+        const uint4 *kp = reinterpret_cast<const uint4 *>(p.deep_keys + 8 * (int64_t)L.ref);
+        const uint4 a = __ldg(kp), b = __ldg(kp + 1);
+        d0 = k0 > a.x ? 1u : 0u;
+        n1 = d0 ? w[2] : w[1];
+        k1 = xr[(n1 & fm) * R];
+        d1 = k1 > (d0 ? a.z : a.y) ? 1u : 0u;
+        n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
+        k2 = xr[(n2 & fm) * R];
+        d2 = k2 > (d0 ? (d1 ? b.z : b.y) : (d1 ? b.x : a.w)) ? 1u : 0u;
+    }
+    const uint32_t e = 4 * d0 + 2 * d1 + d2;
+    const uint32_t mask = w[7] >> 24;
+    if ((mask >> e) & 1u) {
+        L.active = false;
+        int32_t leaf_id = -1;
+        if (MODE == FP_MODE_LEAVES) leaf_id = p.deep_leaf[8 * (int64_t)L.ref + e];
+        const uint32_t cls = MODE == FP_MODE_VALUES ? p.vbase3 + 8 * L.ref + e : (n2 >> (s1 + p.cbits * d2)) & p.cmask;
+        finish<MODE>(p, svotes, row0, L.r, L.t, cls, leaf_id);
+    } else {
+        // children sit side by side from the offset on, in exit order
+        const uint32_t nref = L.ref + (w[7] & FP_DEEP3_OFFSET_MASK) + __popc(~mask & ((1u << e) - 1u));
+        if (nref > L.ref && (int64_t)nref < p.n_super) {  // forward only, so every walk ends
+            L.ref = nref;
+        } else {
+            report(p.status, FP_ERR_FLAG_DEVICE);
+            L.active = false;
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void deep_finish(const TravParams &p, const uint32_t *xs, uint32_t *svotes, int64_t row0,
+                                            LaneTask &L, const uint32_t w[8]) {
+    if (p.deep3) {
+        deep_finish3<MODE>(p, xs, svotes, row0, L, w);
+        return;
+    }
+    const int R = p.R;
+    const uint32_t x0 = xs[(w[3] & 1023u) * R + L.r];
+    const uint32_t d0 = x0 <= w[0] ? 0u : 1u;
     const uint32_t f1 = d0 ? (w[3] >> 20) & 1023u : (w[3] >> 10) & 1023u;
     const uint32_t t1 = d0 ? w[2] : w[1];
-    const float x1 = xs[f1 * R + L.r];
-    const uint32_t d1 = x1 <= __uint_as_float(t1) ? 0u : 1u;
+    const uint32_t x1 = xs[f1 * R + L.r];
+    const uint32_t d1 = x1 <= t1 ? 0u : 1u;
     const uint32_t nref = d0 ? (d1 ? w[7] : w[6]) : (d1 ? w[5] : w[4]);
     if (nref & FP_REF_LEAF) {
         L.active = false;
         int32_t leaf_id = -1;
         if (MODE == FP_MODE_LEAVES) leaf_id = p.deep_leaf[4 * (int64_t)L.ref + 2 * d0 + d1];
         finish<MODE>(p, svotes, row0, L.r, L.t, nref & 0x7FFFFFFFu, leaf_id);
-    } else if (nref > L.ref) {  // super-nodes only point forward, so every walk ends
+    } else if (nref > L.ref && (int64_t)nref < p.n_super) {  // forward only, so every walk ends
         L.ref = nref;
     } else {
         report(p.status, FP_ERR_FLAG_DEVICE);
@@ -282,7 +354,7 @@ template <int MODE>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
     constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
     const int R = p.R, F = p.F, C = p.C;
-    float *xs = reinterpret_cast<float *>(smem);
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // order keys of the tile's rows
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
     const int nbuf = p.nbuf;
     uint8_t *const hbuf0 = smem + xs_bytes;  // nbuf bin-block buffers, head_smem bytes each
@@ -318,10 +390,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     const int nbins = ps.bin_end - ps.bin_begin;
     const float inv_rows = 1.0f / (float)rows;
 
-    // 1. rows (feature-major) -> shared memory; 2. the first bins' blocks in flight
+    // 1. rows (feature-major, as order keys) -> shared memory; 2. the first
+    //    bins' blocks in flight
+    const float *src = p.X + row0 * F;
+    const bool vec_rows = (F & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0;
     {
-        const float *src = p.X + row0 * F;
-        if ((F & 3) == 0 && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0) {
+        if (vec_rows) {
             // lane = row: 16-byte loads along the row, and each store of a
             // warp writes 32 consecutive rows of one feature (32 banks)
             const int nq = F >> 2;
@@ -329,7 +403,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 const int r = g * 32 + lane;
                 if (r < rows) {
                     const float4 *rp = reinterpret_cast<const float4 *>(src + (int64_t)r * F);
-                    float *dst = xs + r;
+                    uint32_t *dst = xs + r;
                     int q = 0;
                     for (; q + 4 <= nq; q += 4) {
                         float4 v[4];
@@ -337,20 +411,20 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                         for (int u = 0; u < 4; ++u) v[u] = __ldg(rp + q + u);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            float *d = dst + (4 * (q + u)) * R;
-                            d[0] = v[u].x;
-                            d[R] = v[u].y;
-                            d[2 * R] = v[u].z;
-                            d[3 * R] = v[u].w;
+                            uint32_t *d = dst + (4 * (q + u)) * R;
+                            d[0] = obs_key(v[u].x);
+                            d[R] = obs_key(v[u].y);
+                            d[2 * R] = obs_key(v[u].z);
+                            d[3 * R] = obs_key(v[u].w);
                         }
                     }
                     for (; q < nq; ++q) {
                         const float4 v = __ldg(rp + q);
-                        float *d = dst + (4 * q) * R;
-                        d[0] = v.x;
-                        d[R] = v.y;
-                        d[2 * R] = v.z;
-                        d[3 * R] = v.w;
+                        uint32_t *d = dst + (4 * q) * R;
+                        d[0] = obs_key(v.x);
+                        d[R] = obs_key(v.y);
+                        d[2 * R] = obs_key(v.z);
+                        d[3 * R] = obs_key(v.w);
                     }
                 }
             }
@@ -371,6 +445,14 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     if (!LEAVES)
         for (int i = tid; i < rows * CS; i += blockDim.x) svotes[i] = 0;
     cp_async_wait_all();
+    if (!vec_rows) {  // each thread turns the values it copied into keys
+        const int total = rows * F;
+        for (int e = tid; e < total; e += blockDim.x) {
+            const int r = e / F;
+            uint32_t *x = xs + (e - r * F) * R + r;
+            *x = obs_key(__uint_as_float(*x));
+        }
+    }
     __syncthreads();
 
     LaneTask L;
@@ -435,26 +517,26 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 const int r2 = my ? task - k2 * rows : 0;
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
-                const float *xr = xs + r2;     // this lane's row
+                const uint32_t *xr = xs + r2;  // this lane's row (keys)
                 if (p.levels == 2) {
                     // paired slots: a node and its two children per 16-byte record,
                     // successors 4q+1 .. 4q+4; (depth+1)/2 records per walk
                     const uint4 *hq = reinterpret_cast<const uint4 *>(blk) + k2;
                     for (int l = 0; l <= p.depth; l += 2) {
                         const uint4 nd = hq[hr * stride];
-                        const float x0 = xr[(nd.w & 1023u) * R];
-                        const uint32_t d0 = x0 <= __uint_as_float(nd.x) ? 0u : 1u;
+                        const uint32_t x0 = xr[(nd.w & 1023u) * R];
+                        const uint32_t d0 = x0 <= nd.x ? 0u : 1u;
                         const uint32_t f1 = d0 ? (nd.w >> 20) & 1023u : (nd.w >> 10) & 1023u;
-                        const float x1 = xr[f1 * R];
-                        const uint32_t d1 = x1 <= __uint_as_float(d0 ? nd.z : nd.y) ? 0u : 1u;
+                        const uint32_t x1 = xr[f1 * R];
+                        const uint32_t d1 = x1 <= (d0 ? nd.z : nd.y) ? 0u : 1u;
                         hr = 4 * hr + 1 + 2 * d0 + d1;
                     }
                 } else if (p.levels) {
                     // implicit slots: every walk takes depth+1 steps, children 2s+1, 2s+2
                     for (int l = 0; l <= p.depth; ++l) {
                         const uint2 nd = hn[hr * stride];
-                        const float xv = xr[(nd.y >> 22) * R];
-                        hr = 2 * hr + (xv <= __uint_as_float(nd.x) ? 1u : 2u);
+                        const uint32_t xv = xr[(nd.y >> 22) * R];
+                        hr = 2 * hr + (xv <= nd.x ? 1u : 2u);
                     }
                 }
                 bool busy = my && !p.levels;
@@ -464,7 +546,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                         if (busy) {
                             const uint2 nd = hn[hr * stride];
                             const uint32_t m = nd.y;
-                            uint32_t nh = xr[(m >> 22) * R] <= __uint_as_float(nd.x)
+                            uint32_t nh = xr[(m >> 22) * R] <= nd.x
                                               ? (m & FP_TARGET_MASK)
                                               : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
                             busy = nh < (uint32_t)nranks;

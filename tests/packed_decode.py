@@ -12,13 +12,39 @@ HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_trees", "<i4"), ("n_fe
                 ("off_bins", "<i8"), ("off_passes", "<i8"), ("off_tree_base", "<i8"), ("off_heads", "<i8"),
                 ("off_deep", "<i8"), ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"),
                 ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8"),
-                ("n_values", "<i8"), ("off_values", "<i8")],
+                ("n_values", "<i8"), ("off_values", "<i8"), ("deep_levels", "<i4"), ("feature_bits", "<i4"),
+                ("class_bits", "<i4"), ("reserved0", "<i4"), ("off_deep_keys", "<i8"), ("values3_base", "<i8")],
                align=True)
 BIN = np.dtype([("head_off", "<u4"), ("head_bytes", "<u4"), ("first_tree", "<i4"), ("width", "<i4"),
                 ("phead_off", "<u4"), ("stride", "<i4"), ("nranks", "<i4"), ("nexits", "<i4")])
 PASS = np.dtype([("bin_begin", "<i4"), ("bin_end", "<i4")])
 
 LEAF = 0x80000000
+
+
+def obs_key(x) -> np.ndarray:
+    """Order keys of observation values: unsigned compares of keys order like
+    the floats (-0 as +0; NaN above everything)."""
+    a = np.asarray(x, dtype=np.float32)
+    u = np.ascontiguousarray(a).reshape(-1).view(np.uint32).copy()
+    nan = (u & 0x7FFFFFFF) > 0x7F800000
+    u[u == 0x80000000] = 0
+    k = np.where(u >> 31 == 1, ~u, u | np.uint32(0x80000000)).astype(np.uint32)
+    k[nan] = 0xFFFFFFFF
+    return k.reshape(a.shape)
+
+
+def thr_key(t) -> np.ndarray:
+    """Order keys of thresholds: as obs_key, but a NaN threshold gets 0 (every
+    observation goes right of it, as x <= NaN never holds)."""
+    k = np.array(obs_key(t))
+    k[np.isnan(np.asarray(t, dtype=np.float32))] = 0
+    return k
+
+
+def _popc8(v: np.ndarray) -> np.ndarray:
+    v = v.astype(np.int64)
+    return sum((v >> i) & 1 for i in range(8))
 
 
 class Image:
@@ -32,27 +58,33 @@ class Image:
         self.tree_base = img[g["off_tree_base"]: g["off_tree_base"] + 4 * g["n_trees"]].view("<u4")
         deep = img[g["off_deep"]: g["off_deep"] + 32 * g["n_super"]]
         self.sw = deep.view("<u4").reshape(-1, 8)          # super-node words
-        self.sthr = deep.view("<f4").reshape(-1, 8)[:, :3]  # thresholds of v, left, right
-        dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 16 * g["n_super"]].view("<i4")
-        self.deep_leaf = dl.reshape(-1, 4)
+        self.sthr = self.sw[:, :3]                         # two levels: keys of v, left, right
+        ne = 8 if g["deep_levels"] == 3 else 4
+        dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 4 * ne * g["n_super"]].view("<i4")
+        self.deep_leaf = dl.reshape(-1, ne)
+        if g["deep_levels"] == 3:
+            dk = img[g["off_deep_keys"]: g["off_deep_keys"] + 32 * g["n_super"]].view("<u4")
+            self.deep_keys = dk.reshape(-1, 8)
+        self.ties = 0  # three levels: compares decided by the full keys in the last walk
         # forests with leaf values: a leaf reference names a slot of this table
         self.values = img[g["off_values"]: g["off_values"] + 4 * g["n_values"]].view("<f4")
 
     def head(self, b: int):
-        """(thr [nranks][stride], meta [nranks][stride], exits [nexits][stride],
-        exit leaf ids [nexits][stride]) of bin b's interleaved block; for
-        paired level heads thr is [nranks][stride][3] (node, left and right
-        child) and meta [nranks][stride] the packed features."""
+        """(threshold keys [nranks][stride], meta [nranks][stride], exits
+        [nexits][stride], exit leaf ids [nexits][stride]) of bin b's
+        interleaved block; for paired level heads thr is [nranks][stride][3]
+        (node, left and right child) and meta [nranks][stride] the packed
+        features."""
         g, bn = self.h, self.bins[b]
         st, nr, ne = int(bn["stride"]), int(bn["nranks"]), int(bn["nexits"])
         base = g["off_heads"] + int(bn["head_off"])
         rec = 16 if g["head_select"] == 2 else 8
         recs = self.img[base: base + rec * nr * st]
         if rec == 16:
-            thr = recs.view("<f4").reshape(nr, st, 4)[:, :, :3]
+            thr = recs.view("<u4").reshape(nr, st, 4)[:, :, :3]
             meta = recs.view("<u4").reshape(nr, st, 4)[:, :, 3]
         else:
-            thr = recs.view("<f4")[0::2].reshape(nr, st)
+            thr = recs.view("<u4")[0::2].reshape(nr, st)
             meta = recs.view("<u4")[1::2].reshape(nr, st)
         exits = self.img[base + rec * nr * st: base + rec * nr * st + 4 * ne * st].view("<u4").reshape(ne, st)
         pb = g["off_pheads"] + int(bn["phead_off"])
@@ -60,8 +92,11 @@ class Image:
         return thr, meta, exits, par
 
     def walk(self, X: np.ndarray):
-        """Leaf id and class per (observation, tree), decoding the records."""
+        """Leaf id and class (or value slot) per (observation, tree), decoding
+        the records; X holds float observations, compared through their keys."""
         g = self.h
+        X = obs_key(X).astype(np.int64)
+        self.ties = 0
         n, T = X.shape[0], g["n_trees"]
         leaf = np.full((n, T), -2, np.int32)
         cls = np.full((n, T), -2, np.int32)
@@ -105,6 +140,15 @@ class Image:
                 while np.any(state == 1):
                     a = rows[state == 1]
                     g_idx = idx[a]
+                    if g["deep_levels"] == 3:
+                        ex, nref, c3 = self._step3(X, a, g_idx)
+                        fin = (nref & LEAF) != 0
+                        fa = a[fin]
+                        cls[fa, t] = c3[fin]
+                        leaf[fa, t] = self.deep_leaf[g_idx[fin], ex[fin]]
+                        state[fa] = 2
+                        idx[a[~fin]] = nref[~fin]
+                        continue
                     w = self.sw[g_idx]
                     th = self.sthr[g_idx]
                     f0 = (w[:, 3] & 1023).astype(np.int64)
@@ -121,3 +165,42 @@ class Image:
                     state[fa] = 2
                     idx[a[~fin]] = nref[~fin]
         return leaf, cls
+
+    def _step3(self, X, a, g_idx):
+        """One three-level super-node per row of a: (exit, next reference or
+        LEAF, class or value slot).  Decides by the key prefixes, checks that
+        wherever the prefixes differ they agree with the full keys, and
+        counts the ties that the full keys decide."""
+        g = self.h
+        fb, cb = g["feature_bits"], g["class_bits"]
+        fm, s2 = (1 << fb) - 1, fb + 2 * cb
+        w = self.sw[g_idx].astype(np.int64)
+        K = self.deep_keys[g_idx].astype(np.int64)
+        ar = np.arange(len(a))
+
+        def level(word, shift, full):
+            k = X[a, word & fm]
+            dp, tie = (k >> shift) > (word >> shift), (k >> shift) == (word >> shift)
+            return k > full, dp, tie
+
+        e0, p0, t0 = level(w[:, 0], fb, K[:, 0])
+        s1 = 1 + e0.astype(np.int64)
+        e1, p1, t1 = level(w[ar, s1], fb, K[ar, s1])
+        s2i = 3 + 2 * e0.astype(np.int64) + e1
+        e2, p2, t2 = level(w[ar, s2i], s2, K[ar, s2i])
+        # along the exact path, a prefix that differs from the observation's
+        # must decide as the full key does; the kernel's prefix walk follows
+        # this path up to its first tie, so it sees a tie exactly where this does
+        ok = (t0 | (p0 == e0)) & (t1 | (p1 == e1)) & (t2 | (p2 == e2))
+        assert np.all(ok), "a key prefix decided against the full key"
+        self.ties += int(np.sum(t0 | t1 | t2))
+        ex = 4 * e0.astype(np.int64) + 2 * e1.astype(np.int64) + e2.astype(np.int64)
+        mask = w[:, 7] >> 24
+        is_leaf = ((mask >> ex) & 1) == 1
+        nref = g_idx.astype(np.int64) + (w[:, 7] & 0xFFFFFF) + _popc8(~mask & ((1 << ex) - 1))
+        nref = np.where(is_leaf, LEAF, nref)
+        if g["n_values"]:
+            c3 = g["values3_base"] + 8 * g_idx.astype(np.int64) + ex
+        else:
+            c3 = (w[ar, s2i] >> (fb + cb * e2.astype(np.int64))) & ((1 << cb) - 1)
+        return ex, nref, c3.astype(np.int32)

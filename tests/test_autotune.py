@@ -19,14 +19,16 @@ def test_block_bytes_formula():
 
 def test_candidate_layouts_pack(tiny_forest):
     cands = at.candidate_layouts(tiny_forest.n_trees)
-    assert 2 <= len(cands) <= 16
-    assert {sel for _, _, sel in cands} == {1, 2, 3}
+    assert 2 <= len(cands) <= 17
+    assert {c[2] for c in cands} == {1, 2, 3}
+    assert [c[3] for c in cands if len(c) > 3] == [2]  # one two-level candidate beside the defaults
     assert len(at.candidate_layouts(tiny_forest.n_trees, max_layouts=5)) <= 5
-    for B, d, sel in cands:
+    for c in cands:
+        B, d, sel = c[:3]
         assert 1 <= B <= tiny_forest.n_trees and 0 <= d <= (9 if sel == 3 else 11)
         assert at.block_bytes(B, d, sel) <= 48 * 1024 or d == 0
         assert sel != 2 or d % 2 == 1
-        fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
+        fp.fp_pack_forest(tiny_forest, **dict(zip(at.LAYOUT_KEYS, c)))
 
 
 def test_candidate_launches():

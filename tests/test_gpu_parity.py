@@ -52,19 +52,33 @@ def _check_all(forest, X, ref=None, **params):
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 1, 3), (3, 3, 3), (1, 0, 1), (2, 3, 1), (1, 1, 2), (3, 3, 2),
                                      (3, 9, 0)])
-def test_hand_fixtures_on_gpu(name, B, d, sel):
+@pytest.mark.parametrize("dl", [2, 3])
+def test_hand_fixtures_on_gpu(name, B, d, sel, dl):
     """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs; ranked
-    heads (sel 0) and level heads (sel 1)."""
+    heads (sel 3), level heads (sel 1) and paired level heads (sel 2); super-
+    nodes of two and three levels."""
     forest, X, exp = load(name)
     ref = dict(leaf=exp["leaf"], votes=exp["votes"], cls=exp["cls"])
-    _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel)
+    _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
 
 
 @pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (1, 0, 3), (5, 2, 3), (7, 6, 3), (4, 9, 3), (16, 4, 1), (1, 0, 1),
                                      (3, 8, 1), (1, 11, 1), (16, 5, 2), (4, 9, 2), (1, 11, 2), (2, 1, 2)])
-def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel):
+@pytest.mark.parametrize("dl", [2, 3])
+def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel, dl):
     X, _ = tiny_rows
-    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel)
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+
+
+@pytest.mark.parametrize("B,d,sel", [(4, 2, 1), (3, 1, 2), (2, 3, 3), (1, 0, 1)])
+@pytest.mark.parametrize("dl", [2, 3])
+def test_rows_on_thresholds(tiny_forest, tiny_rows, B, d, sel, dl):
+    """Observations on the forest's thresholds (exactly, or one float step
+    off) and -0, infinities and NaN: with three-level super-nodes many
+    compares tie on the key prefix and are decided by the full keys."""
+    from edge_rows import rows_on_thresholds
+    X = rows_on_thresholds(tiny_forest, tiny_rows[0], seed=12)
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
 
 
 @pytest.mark.parametrize("tile,warps", [(32, 1), (64, 3), (256, 8), (1024, 32)])
@@ -168,3 +182,10 @@ def test_image_workload_params_grid():
     for B, d, sel, nb in [(128, 1, 3, 3), (16, 3, 3, 3), (8, 5, 3, 3), (1, 9, 3, 3), (16, 5, 1, 3), (1, 10, 1, 3),
                           (4, 7, 2, 3), (1, 11, 2, 2)]:
         _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, bin_buffers=nb)
+    # three-level super-nodes with 10 feature and 2 x 4 class bits: 14-bit key
+    # prefixes in the last level, so ties are frequent
+    for B, d, sel in [(16, 3, 2), (4, 6, 1)]:
+        _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=3)
+    from edge_rows import rows_on_thresholds
+    Xe = rows_on_thresholds(forest, X[:1000], seed=13)
+    _check_all(forest, Xe, None, bin_size=16, interleave_depth=3, head_select=2, deep_levels=3)

@@ -12,7 +12,7 @@ import datagen
 import oracle
 import paper_1806_07300_gb300 as fp
 from golden_io import load
-from packed_decode import Image, LEAF
+from packed_decode import Image, LEAF, thr_key
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -41,19 +41,22 @@ def test_binding_has_no_cpu_path():
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 0, 3), (2, 1, 3), (3, 2, 3), (1, 5, 3), (1, 0, 1), (2, 1, 1),
                                      (3, 4, 1), (1, 1, 2), (2, 3, 2)])
-def test_packed_records_decode_to_fixture_leaves(name, B, d, sel):
+@pytest.mark.parametrize("dl", [2, 3])
+def test_packed_records_decode_to_fixture_leaves(name, B, d, sel, dl):
     forest, X, exp = load(name)
-    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel)
+    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
     leaf, cls = Image(pk.image()).walk(X)
     np.testing.assert_array_equal(leaf, exp["leaf"])
 
 
 @pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (5, 0, 3), (1, 2, 3), (7, 7, 3), (16, 4, 1), (3, 0, 1), (1, 9, 1),
                                      (1, 11, 1), (3, 1, 2), (4, 9, 2), (1, 11, 2), (16, 5, 2)])
-def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel):
+@pytest.mark.parametrize("dl", [2, 3])
+def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel, dl):
     X, _ = tiny_rows
     ref = oracle.predict(tiny_forest, X[:3000])
-    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel)
+    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    assert pk.info()["deep_levels"] == dl
     leaf, cls = Image(pk.image()).walk(X[:3000])
     np.testing.assert_array_equal(leaf, ref["leaf"])
     np.testing.assert_array_equal(cls, tiny_forest.leaf_class[tiny_forest.node_begin[:-1][None, :] + ref["leaf"]])
@@ -75,7 +78,7 @@ def _head_nodes(forest, t, im):
             continue
         v = rank_node[r]
         m = int(meta[r, k])
-        assert m >> 22 == tr["feature"][v] and thr[r, k] == tr["threshold"][v]
+        assert m >> 22 == tr["feature"][v] and thr[r, k] == thr_key(tr["threshold"][v])
         for c, tgt in ((int(tr["left"][v]), m & 2047), (int(tr["right"][v]), (m >> 11) & 2047)):
             if tgt < nr:
                 assert tr["left"][c] >= 0, "a head target is an internal node"
@@ -154,7 +157,7 @@ def test_head_select_levels(tiny_forest, d):
             v = slot[s]
             leaf = tr["left"][v] < 0
             if not leaf:
-                assert meta[s, k] >> 22 == tr["feature"][v] and thr[s, k] == tr["threshold"][v]
+                assert meta[s, k] >> 22 == tr["feature"][v] and thr[s, k] == thr_key(tr["threshold"][v])
                 assert meta[s, k] & ((1 << 22) - 1) == 0
             kids = (v, v) if leaf else (int(tr["left"][v]), int(tr["right"][v]))
             for q, c in enumerate(kids):
@@ -166,7 +169,8 @@ def test_head_select_levels(tiny_forest, d):
                 assert ref == LEAF | int(tr["leaf_class"][v]) and par[e, k] == v
             else:
                 assert not ref & LEAF and par[e, k] == -1
-                assert im.sthr[ref, 0] == tr["threshold"][v], "the exit roots the super-node of its node"
+                root_key = im.deep_keys[ref, 0] if im.h["deep_levels"] == 3 else im.sthr[ref, 0]
+                assert root_key == thr_key(tr["threshold"][v]), "the exit roots the super-node of its node"
 
 
 def test_stat_order_in_super_nodes(tiny_forest):
@@ -174,7 +178,7 @@ def test_stat_order_in_super_nodes(tiny_forest):
     reached child super-node (Section III-A, Stat), and every internal node
     lies in the head or in exactly one super-node."""
     f = tiny_forest
-    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=2, head_select=3)
+    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=2, head_select=3, deep_levels=2)
     im = Image(pk.image())
     total = 0
     for t in range(f.n_trees):
@@ -212,7 +216,7 @@ def test_head_interleaving_roots_contiguous(tiny_forest):
         for k in range(int(im.bins[b]["width"])):
             root = int(f.node_begin[first + k])
             assert meta[0, k] >> 22 == f.feature[root]
-            assert thr[0, k] == f.threshold[root]
+            assert thr[0, k] == thr_key(f.threshold[root])
 
 
 def test_pack_info_sizes(tiny_forest):
@@ -223,6 +227,9 @@ def test_pack_info_sizes(tiny_forest):
     assert info["n_bins"] == 1 and info["passes"] == 1
     assert info["bin_buffers"] == 3
     assert fp.fp_pack_forest(tiny_forest, bin_buffers=2).info()["bin_buffers"] == 2
+    # 16 features and 4 classes take 4 + 2 * 2 bits: three levels by default
+    assert info["deep_levels"] == 3
+    assert fp.fp_pack_forest(tiny_forest, deep_levels=2).info()["deep_levels"] == 2
 
 
 def test_passes_split_by_budget(tiny_forest):
@@ -271,7 +278,8 @@ def test_unsupported_sizes_rejected():
 @pytest.mark.parametrize("kw", [dict(bin_size=-1), dict(interleave_depth=12), dict(interleave_depth=12, head_select=1),
                                 dict(obs_tile=33), dict(warps_per_cta=40),
                                 dict(bin_buffers=1), dict(bin_buffers=4), dict(head_select=2, interleave_depth=8),
-                                dict(head_select=4), dict(head_select=3, interleave_depth=10)])
+                                dict(head_select=4), dict(head_select=3, interleave_depth=10),
+                                dict(deep_levels=1), dict(deep_levels=4)])
 def test_bad_params_rejected(tiny_forest, kw):
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(tiny_forest, **kw)
@@ -290,7 +298,8 @@ def test_null_arguments_rejected():
 
 
 @pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 3), (3, 6, 3), (2, 9, 1), (3, 9, 0)])
-def test_value_forest_records_decode_to_oracle(B, d, sel):
+@pytest.mark.parametrize("dl", [2, 3])
+def test_value_forest_records_decode_to_oracle(B, d, sel, dl):
     """A forest with leaf values: every leaf reference names a value slot
     holding the leaf's value, and the walk reaches the oracle's leaves."""
     import datagen
@@ -298,8 +307,10 @@ def test_value_forest_records_decode_to_oracle(B, d, sel):
     F = datagen.train_regression(X, y, 6, mtry=9, min_leaf=3, seed=21, threads=4)
     Xt, _ = datagen.gen_regression(21, 1500, 1, 1.0, 1.0)
     ref = oracle.predict_values(F, Xt)
-    im = Image(fp.fp_pack_forest(F, bin_size=B, interleave_depth=d, head_select=sel).image())
-    assert im.h["n_values"] == int((F.left < 0).sum())
+    im = Image(fp.fp_pack_forest(F, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl).image())
+    n_leaves = int((F.left < 0).sum())
+    assert im.h["values3_base"] == n_leaves
+    assert im.h["n_values"] == n_leaves + (8 * im.h["n_super"] if dl == 3 else 0)
     leaf, slot = im.walk(Xt)
     np.testing.assert_array_equal(leaf, ref["leaf"])
     np.testing.assert_array_equal(im.values[slot], F.leaf_value[F.node_begin[:-1][None, :] + ref["leaf"]])
@@ -314,3 +325,111 @@ def test_value_forest_rejects_non_finite_values():
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(F)
     assert ei.value.code == fp.FP_EINVAL
+
+
+@pytest.mark.parametrize("dl", [2, 3])
+@pytest.mark.parametrize("sel", [1, 3])
+def test_rows_on_thresholds_decode_to_oracle_leaves(tiny_forest, tiny_rows, dl, sel):
+    """Observations equal to the forest's thresholds (or one float step off),
+    and -0, infinities and NaN: the key compares give the oracle's leaves,
+    and with three-level super-nodes the key-prefix ties are decided by the
+    full keys (many of them occur here)."""
+    from edge_rows import rows_on_thresholds
+    X = rows_on_thresholds(tiny_forest, tiny_rows[0][:3000], seed=11)
+    ref = oracle.predict(tiny_forest, X)
+    im = Image(fp.fp_pack_forest(tiny_forest, bin_size=4, interleave_depth=2, head_select=sel,
+                                 deep_levels=dl).image())
+    leaf, cls = im.walk(X)
+    np.testing.assert_array_equal(leaf, ref["leaf"])
+    if dl == 3:
+        assert im.ties > 100
+
+
+def test_key_order_matches_float_compare():
+    """x <= t exactly when key(x) <= key(t), over values that stress the map:
+    signed zeros, subnormals, infinities, neighbours of each other; a NaN x
+    goes right of every threshold, and every x goes right of a NaN threshold."""
+    from packed_decode import obs_key
+    v = np.array([0.0, -0.0, 1e-45, -1e-45, 1.17549435e-38, -1.17549435e-38, 1.0, -1.0, 3.4028235e38,
+                  -3.4028235e38, np.inf, -np.inf, 0.5, np.nextafter(np.float32(0.5), np.float32(1)),
+                  np.nextafter(np.float32(0.5), np.float32(0))], dtype=np.float32)
+    kx, kt = obs_key(v), thr_key(v)
+    for i in range(v.size):
+        for j in range(v.size):
+            assert (kx[i] <= kt[j]) == bool(v[i] <= v[j]), (v[i], v[j])
+    nan = np.array([np.nan, -np.nan], dtype=np.float32)
+    assert np.all(obs_key(nan)[:, None] > kt[None, :])
+    assert np.all(kx[:, None] > thr_key(nan)[None, :])
+
+
+def test_three_level_super_nodes(tiny_forest):
+    """Three-level super-nodes (format in fp_internal.h): seven slots holding
+    the node, its children and grandchildren (a leaf carried down as
+    dummies), key prefixes and features in the words, full keys in the side
+    table, leaf mask, classes and leaf ids of the eight exits, and the
+    children side by side in exit order; a super-node whose children have
+    their own children expands the most frequently reached one first (Stat);
+    every internal node lies in the head or in exactly one super-node."""
+    f = tiny_forest
+    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=1, head_select=1, deep_levels=3)
+    im = Image(pk.image())
+    fb, cb = im.h["feature_bits"], im.h["class_bits"]
+    assert (fb, cb) == (4, 2)
+    covered = 0
+    for t in range(f.n_trees):
+        tr = f.tree(t)
+        thr, meta, exits, par = im.head(t // 4)
+        k = t % 4
+        covered += sum(1 for s in range(thr.shape[0]) if meta[s, k] or thr[s, k])  # head slots that split
+        stack = [(int(exits[e, k]), None) for e in range(exits.shape[0]) if not int(exits[e, k]) & LEAF]
+        # recover each super-node's root: the head exit's node
+        slot = {0: 0}
+        for s in range(thr.shape[0]):
+            v = slot[s]
+            kids = (v, v) if tr["left"][v] < 0 else (int(tr["left"][v]), int(tr["right"][v]))
+            slot[2 * s + 1], slot[2 * s + 2] = kids
+        todo = [(int(exits[e, k]), slot[thr.shape[0] + e]) for e in range(exits.shape[0])
+                if not int(exits[e, k]) & LEAF]
+        seen = set()
+        while todo:
+            g, v = todo.pop()
+            assert g not in seen
+            seen.add(g)
+            w = [int(x) for x in im.sw[g]]
+            sl = [v]
+            for i in range(3):
+                u = sl[i]
+                sl += [u, u] if tr["left"][u] < 0 else [int(tr["left"][u]), int(tr["right"][u])]
+            ex = []
+            for i in range(3, 7):
+                u = sl[i]
+                ex += [u, u] if tr["left"][u] < 0 else [int(tr["left"][u]), int(tr["right"][u])]
+            for i, u in enumerate(sl):
+                sh = fb if i < 3 else fb + 2 * cb
+                if tr["left"][u] < 0:
+                    assert w[i] >> sh == 0 and im.deep_keys[g, i] == 0
+                    continue
+                covered += 1
+                key = int(thr_key(tr["threshold"][u]))
+                assert im.deep_keys[g, i] == key and w[i] >> sh == key >> sh
+                assert w[i] & ((1 << fb) - 1) == tr["feature"][u]
+            mask = w[7] >> 24
+            first = g + (w[7] & 0xFFFFFF)
+            rank = 0
+            kids = []
+            for e, c in enumerate(ex):
+                if tr["left"][c] < 0:
+                    assert (mask >> e) & 1 and im.deep_leaf[g, e] == c
+                    assert (w[3 + e // 2] >> (fb + cb * (e & 1))) & ((1 << cb) - 1) == tr["leaf_class"][c]
+                else:
+                    assert not (mask >> e) & 1 and im.deep_leaf[g, e] == -1
+                    kids.append((first + rank, c))
+                    rank += 1
+            todo += kids
+            # Stat: of the children that have children, the most visited one's block comes first
+            firsts = [(int(im.sw[gc, 7]) & 0xFFFFFF and gc + (int(im.sw[gc, 7]) & 0xFFFFFF), c) for gc, c in kids]
+            firsts = [(fs, c) for fs, c in firsts if fs]
+            if len(firsts) > 1:
+                hot = max(firsts, key=lambda z: (int(tr["cardinality"][z[1]]), -z[0]))
+                assert hot[0] == min(fs for fs, _ in firsts)
+    assert covered == pk.info()["n_internal"]
