@@ -109,11 +109,12 @@ typedef struct fp_forest_desc {
  *                     2 or 3 (0 = 3): two leave room for larger heads or
  *                     tiles, three hide copy latency better
  *   deep_levels       tree levels per 32-byte super-node below the head: 2
- *                     (full thresholds), 3 (thresholds shortened to key
- *                     prefixes, ties decided by a side table of full keys;
- *                     needs ceil(log2 F) + 2 * ceil(log2 C) <= 24, classes
- *                     not counted for forests with leaf values), or
- *                     0 = default: 3 when that sum is at most 12, else 2 */
+ *                     (full thresholds), 3 (the last level's thresholds
+ *                     shortened to key prefixes, ties decided by a side
+ *                     table of full keys; needs 2 * ceil(log2 F) +
+ *                     2 * ceil(log2 C) <= 24, classes not counted for
+ *                     forests with leaf values), or 0 = default: 3 when that
+ *                     sum is at most 16, else 2 */
 typedef struct fp_pack_params {
     int32_t bin_size;
     int32_t interleave_depth;

@@ -89,16 +89,19 @@ size_t smem_bytes(int R, int F, int head_smem, int nbuf, int C, int warps, bool 
     return xs + (size_t)nbuf * (size_t)head_smem + votes + (size_t)warps * FP_RING * 8;
 }
 
-// The kernel variant for a block size: up to 512 threads run the three-CTAs-
-// per-SM build (<= 42 registers), larger blocks the one-CTA build.
+// The kernel variant for a forest and block size: its kind of super-node
+// (two or three levels), and up to 768 threads run the build for several CTAs
+// per SM (<= 42 registers), larger blocks the one-CTA build.
 template <int MODE>
-void (*traverse_kernel(int threads))(TravParams) {
-    return threads <= 512 ? fp_traverse_kernel<MODE, 3> : fp_traverse_kernel<MODE, 1>;
+void (*traverse_kernel(const fp_device_forest *f))(TravParams) {
+    if (f->hdr.deep_levels == 3)
+        return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, true> : fp_traverse_kernel<MODE, 1, true>;
+    return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, false> : fp_traverse_kernel<MODE, 1, false>;
 }
 
 template <int MODE>
 int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
-    auto kern = traverse_kernel<MODE>(f->threads);
+    auto kern = traverse_kernel<MODE>(f);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
@@ -207,7 +210,7 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     if (p.deep3) {
         p.fbits = (uint32_t)h.feature_bits;
         p.cbits = (uint32_t)h.class_bits;
-        p.sh2 = p.fbits + 2 * p.cbits;
+        p.sh2 = 2 * p.fbits + 2 * p.cbits;
         p.fmask = (1u << p.fbits) - 1u;
         p.cmask = (1u << p.cbits) - 1u;
         p.vbase3 = (uint32_t)h.values3_base;
@@ -338,7 +341,7 @@ extern "C" int fp_predict(const fp_device_forest *f, const float *X, int64_t n, 
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    traverse_kernel<FP_MODE_VOTES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<FP_MODE_VOTES>(f)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (scratch) cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
@@ -380,7 +383,7 @@ extern "C" int fp_predict_values(const fp_device_forest *f, const float *X, int6
         p.tile_done = reinterpret_cast<uint32_t *>(sc + acc_bytes);
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_values);
-    traverse_kernel<FP_MODE_VALUES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_values, s>>>(p);
+    traverse_kernel<FP_MODE_VALUES>(f)<<<(unsigned)grid, f->threads, f->smem_values, s>>>(p);
     e = cudaGetLastError();
     if (scratch) cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<values> launch");
@@ -464,7 +467,7 @@ extern "C" int fp_predict_noalloc(const fp_device_forest *f, const float *X, int
         }
     }
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_votes);
-    traverse_kernel<FP_MODE_VOTES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
+    traverse_kernel<FP_MODE_VOTES>(f)<<<(unsigned)grid, f->threads, f->smem_votes, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel launch");
     return FP_OK;
@@ -485,7 +488,7 @@ extern "C" int fp_predict_leaves(const fp_device_forest *f, const float *X, int6
     p.n_items = p.n_tiles * f->hdr.n_passes;
     p.out_leaf = out_leaf;
     const int64_t grid = std::min<int64_t>(p.n_items, f->grid_leaves);
-    traverse_kernel<FP_MODE_LEAVES>(f->threads)<<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
+    traverse_kernel<FP_MODE_LEAVES>(f)<<<(unsigned)grid, f->threads, f->smem_leaves, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fp_traverse_kernel<leaves> launch");
     return FP_OK;

@@ -15,8 +15,8 @@
 //                                    exit[e*stride + k]   = e-th exit of tree k
 //   deep     FpSuper[]           per tree, its super-nodes in Stat order; the
 //                                trees' regions follow one another
-//   deep_keys uint32[8] per super-node (three-level super-nodes only): the
-//                                full keys of its seven nodes (slot 7 zero)
+//   deep_keys uint32[4] per super-node (three-level super-nodes only): the
+//                                full keys of its last level (slots 3..6)
 //   values   float[n_values]     forests with leaf values (see below)
 //   --- end of the classification part (class_bytes) ---
 //   parity blocks                per bin, int32 leaf id of each exit (or -1),
@@ -91,19 +91,22 @@
 // dummies, like the level heads) and eight exits (exit e is child e & 1 of
 // slot 3 + (e >> 1)) -- three levels per load.  With fb = feature_bits and
 // cb = class_bits:
-//   w[0..2] slots 0..2: [31:fb] the top 32-fb bits of the key, [fb-1:0] feature
-//   w[3..6] slots 3..6: [31:fb+2cb] the top 32-fb-2cb bits of the key,
-//           [fb+2cb-1:fb+cb] class of the right exit, [fb+cb-1:fb] class of
-//           the left exit (a leaf exit's class; 0 otherwise), [fb-1:0] feature
+//   w[0..2] the full keys of slots 0..2
+//   w[3..6] slots 3..6: [fb-1:0] feature, [2fb-1:fb] the feature of slot
+//           0, 1, 2 (in w[3], w[4], w[5]; zero in w[6]), [2fb+2cb-1:2fb+cb]
+//           class of the right exit and [2fb+cb-1:2fb] of the left one (a
+//           leaf exit's class; 0 otherwise), [31:2fb+2cb] the top bits of
+//           the slot's key
 //   w[7]    [31:24] leaf mask (bit e set: exit e is a leaf),
 //           [23:0]  offset from this super-node to the first of its children:
 //           the super-nodes rooted at its internal exits are consecutive, in
 //           exit order, so exit e continues at this + offset + (number of
 //           internal exits before e)
-// The walk compares the key of x with a key prefix; when the prefixes are
-// equal it decides with the full key from deep_keys (one more load, for a
-// small fraction of compares).  A dummy slot has key 0 (never a tie).  In a
-// forest with leaf values exit e of super-node g names the value slot
+// The first two levels compare full keys; the last compares the key of x
+// with a key prefix, and when the prefixes are equal it decides with the full
+// key from deep_keys (a 4-byte load, for a small fraction of compares).  A
+// dummy slot has key 0 (every observation goes right of it, never a tie).
+// In a forest with leaf values exit e of super-node g names the value slot
 // values3_base + 8g + e.
 #pragma once
 #include <stdint.h>
@@ -160,6 +163,6 @@ struct FpImageHeader {
     int32_t deep_levels;           // 2 or 3 tree levels per super-node
     int32_t feature_bits, class_bits;  // three-level super-nodes: field widths fb, cb
     int32_t reserved0;
-    int64_t off_deep_keys;         // three-level super-nodes: full keys, 8 per super-node
+    int64_t off_deep_keys;         // three-level super-nodes: full keys of the last level, 4 per super-node
     int64_t values3_base;          // forests with leaf values: first slot of the per-exit values
 };

@@ -382,22 +382,27 @@ void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t ba
     }
 }
 
-// A three-level super-node (format in fp_internal.h): key prefixes and
-// features of its seven slots, leaf classes in the last level's words, the
-// leaf mask and the offset to its first child; the full keys, the leaf ids
-// and (forests with leaf values) the exits' values go to side tables.
+// A three-level super-node (format in fp_internal.h): full keys of the first
+// two levels, then per last-level slot its feature, one upper slot's
+// feature, its exits' classes and its key prefix; the leaf mask and the
+// offset to the first child.  The last level's full keys, the leaf ids and
+// (forests with leaf values) the exits' values go to side tables.
 void encode_super3(const TreeRef &t, const TreeLayout &lay, int32_t v, int32_t fb, int32_t cb, const float *leaf_value,
-                   FpSuper &sn, uint32_t keys[8], int32_t leaf_ids[8], float *vals) {
+                   FpSuper &sn, uint32_t keys[4], int32_t leaf_ids[8], float *vals) {
     int32_t sl[7], e[8];
     slots3(t, v, sl, e);
+    auto feat = [&](int32_t u) { return t.leaf(u) ? 0u : (uint32_t)t.Fe[u]; };
+    const int32_t sh = 2 * fb + 2 * cb;
     for (int i = 0; i < 7; ++i) {
         const int32_t u = sl[i];
         const uint32_t key = t.leaf(u) ? 0u : thr_key(t.Th[u]);
-        const int32_t sh = i < 3 ? fb : fb + 2 * cb;
-        keys[i] = key;
-        sn.w[i] = (key & ~((1u << sh) - 1u)) | (t.leaf(u) ? 0u : (uint32_t)t.Fe[u]);
+        if (i < 3) {
+            sn.w[i] = key;
+            continue;
+        }
+        keys[i - 3] = key;
+        sn.w[i] = (key & ~((1u << sh) - 1u)) | feat(u) | (i < 6 ? feat(sl[i - 3]) << fb : 0u);
     }
-    keys[7] = 0;
     uint32_t mask = 0;
     for (int q = 0; q < 8; ++q) {
         const int32_t c = e[q];
@@ -406,7 +411,7 @@ void encode_super3(const TreeRef &t, const TreeLayout &lay, int32_t v, int32_t f
         if (!t.leaf(c)) continue;
         mask |= 1u << q;
         leaf_ids[q] = c;
-        if (cb) sn.w[3 + q / 2] |= (uint32_t)t.Cl[c] << (fb + cb * (q & 1));
+        if (cb) sn.w[3 + q / 2] |= (uint32_t)t.Cl[c] << (2 * fb + cb * (q & 1));
         if (vals) vals[q] = leaf_value[c];
     }
     const int32_t first = lay.sn_first[lay.sn_index[v]];
@@ -447,7 +452,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const bool paired = kind == 2;
     // three-level super-nodes: feature and class fields beside the key prefixes
     const int32_t fb = bits_for(F), cb = desc->leaf_value ? 0 : (C > 1 ? bits_for(C) : 0);
-    const bool three = p.deep_levels == 3 || (p.deep_levels == 0 && fb + 2 * cb <= 12);
+    const bool three = p.deep_levels == 3 || (p.deep_levels == 0 && 2 * fb + 2 * cb <= 16);
     int32_t R = p.obs_tile;
     if (R == 0) {  // rows take up to ~96 KiB of shared memory
         int64_t r = (96 * 1024) / ((int64_t)F * 4);
@@ -465,7 +470,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                      p.head_select, p.bin_buffers, p.deep_levels);
         return FP_EINVAL;
     }
-    if (three && fb + 2 * cb > 24) {
+    if (three && 2 * fb + 2 * cb > 24) {
         fp_set_error("fp_pack_forest: %d features and %d classes leave three-level super-nodes too few key bits; "
                      "use deep_levels = 2", F, C);
         return FP_EUNSUPPORTED;
@@ -611,7 +616,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.deep_levels = three ? 3 : 2;
         h.feature_bits = three ? fb : 0;
         h.class_bits = three ? cb : 0;
-        h.off_deep_keys = off; off = align_up(off + (three ? 32 * n_deep : 0), 256);
+        h.off_deep_keys = off; off = align_up(off + (three ? 16 * n_deep : 0), 256);
         h.n_values = n_values;
         h.values3_base = values3_base;
         h.off_values = off; off = align_up(off + 4 * n_values, 256);
@@ -743,7 +748,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             for (size_t i = 0; i < lay.sn_root.size(); ++i) {
                 const int64_t g = tree_base[t] + (int64_t)i;
                 if (three) {
-                    uint32_t *keys = reinterpret_cast<uint32_t *>(img + h.off_deep_keys) + 8 * g;
+                    uint32_t *keys = reinterpret_cast<uint32_t *>(img + h.off_deep_keys) + 4 * g;
                     float *vals = desc->leaf_value
                                       ? reinterpret_cast<float *>(img + h.off_values) + values3_base + 8 * g
                                       : nullptr;

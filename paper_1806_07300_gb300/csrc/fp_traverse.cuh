@@ -90,10 +90,10 @@ struct TravParams {
     int32_t spin_limit;       // polls of a bin block's barrier before the wait gives up
     int32_t stall;            // fault injection: bin waits ignore completed copies (0 normally)
     int32_t deep3;            // super-nodes of three levels (else two)
-    uint32_t fbits, sh2;      // three levels: feature bits; key-prefix shift of the last level
+    uint32_t fbits, sh2;      // three levels: feature bits; key-prefix shift of the last level (2fb + 2cb)
     uint32_t cbits, fmask, cmask;  // three levels: class bits, feature and class masks
     uint32_t vbase3;          // three levels, values mode: first per-exit value slot
-    const uint32_t *deep_keys;  // three levels: full keys, 8 per super-node
+    const uint32_t *deep_keys;  // three levels: full keys of the last level, 4 per super-node
     int64_t n_super;
 };
 
@@ -230,43 +230,32 @@ __device__ __forceinline__ void deep_issue(const TravParams &p, const LaneTask &
     ld_super(p.deep + L.ref, w);
 }
 
-// Three levels: the key of x against each slot's key prefix; a tie of the
-// prefixes (rare) is decided again from the full keys of the super-node.
+// Three levels: full keys for the first two, and a key prefix for the last,
+// whose tie (rare) is decided by the slot's full key from the side table.
 template <int MODE>
 __device__ __forceinline__ void deep_finish3(const TravParams &p, const uint32_t *xs, uint32_t *svotes, int64_t row0,
                                              LaneTask &L, const uint32_t w[8]) {
     const uint32_t *xr = xs + L.r;
     const int R = p.R;
-    const uint32_t fm = p.fmask, s1 = p.fbits, s2 = p.sh2;
-    const uint32_t k0 = xr[(w[0] & fm) * R];
-    uint32_t d0 = (k0 >> s1) > (w[0] >> s1) ? 1u : 0u;
-    bool tie = (k0 >> s1) == (w[0] >> s1);
-    uint32_t n1 = d0 ? w[2] : w[1];
-    uint32_t k1 = xr[(n1 & fm) * R];
-    uint32_t d1 = (k1 >> s1) > (n1 >> s1) ? 1u : 0u;
-    tie |= (k1 >> s1) == (n1 >> s1);
-    uint32_t n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
-    uint32_t k2 = xr[(n2 & fm) * R];
+    const uint32_t fm = p.fmask, fb = p.fbits, s2 = p.sh2;
+    const uint32_t k0 = xr[((w[3] >> fb) & fm) * R];
+    const uint32_t d0 = k0 > w[0] ? 1u : 0u;
+    const uint32_t n1 = d0 ? w[2] : w[1];
+    const uint32_t k1 = xr[(((d0 ? w[5] : w[4]) >> fb) & fm) * R];
+    const uint32_t d1 = k1 > n1 ? 1u : 0u;
+    const uint32_t j = 2 * d0 + d1;  // last-level slot 3 + j
+    const uint32_t n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
+    const uint32_t k2 = xr[(n2 & fm) * R];
     uint32_t d2 = (k2 >> s2) > (n2 >> s2) ? 1u : 0u;
-    tie |= (k2 >> s2) == (n2 >> s2);
-    if (tie) {
-        const uint4 *kp = reinterpret_cast<const uint4 *>(p.deep_keys + 8 * (int64_t)L.ref);
-        const uint4 a = __ldg(kp), b = __ldg(kp + 1);
-        d0 = k0 > a.x ? 1u : 0u;
-        n1 = d0 ? w[2] : w[1];
-        k1 = xr[(n1 & fm) * R];
-        d1 = k1 > (d0 ? a.z : a.y) ? 1u : 0u;
-        n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
-        k2 = xr[(n2 & fm) * R];
-        d2 = k2 > (d0 ? (d1 ? b.z : b.y) : (d1 ? b.x : a.w)) ? 1u : 0u;
-    }
-    const uint32_t e = 4 * d0 + 2 * d1 + d2;
+    if ((k2 >> s2) == (n2 >> s2)) d2 = k2 > __ldg(p.deep_keys + 4 * (int64_t)L.ref + j) ? 1u : 0u;
+    const uint32_t e = 2 * j + d2;
     const uint32_t mask = w[7] >> 24;
     if ((mask >> e) & 1u) {
         L.active = false;
         int32_t leaf_id = -1;
         if (MODE == FP_MODE_LEAVES) leaf_id = p.deep_leaf[8 * (int64_t)L.ref + e];
-        const uint32_t cls = MODE == FP_MODE_VALUES ? p.vbase3 + 8 * L.ref + e : (n2 >> (s1 + p.cbits * d2)) & p.cmask;
+        const uint32_t cls =
+            MODE == FP_MODE_VALUES ? p.vbase3 + 8 * L.ref + e : (n2 >> (2 * fb + p.cbits * d2)) & p.cmask;
         finish<MODE>(p, svotes, row0, L.r, L.t, cls, leaf_id);
     } else {
         // children sit side by side from the offset on, in exit order
@@ -280,10 +269,12 @@ __device__ __forceinline__ void deep_finish3(const TravParams &p, const uint32_t
     }
 }
 
-template <int MODE>
+// D3: the forest's super-nodes have three levels (p.deep3), else two; a
+// compile-time choice, so neither kind's step carries the other's code.
+template <int MODE, bool D3>
 __device__ __forceinline__ void deep_finish(const TravParams &p, const uint32_t *xs, uint32_t *svotes, int64_t row0,
                                             LaneTask &L, const uint32_t w[8]) {
-    if (p.deep3) {
+    if (D3) {
         deep_finish3<MODE>(p, xs, svotes, row0, L, w);
         return;
     }
@@ -350,7 +341,7 @@ __device__ __forceinline__ void cta_finish(CtaShared &sh) {
 // completes its barrier's phase k, so a wait needs the buffer's copy count
 // at the item's start (use0) plus bi / nbuf.  Counting per buffer keeps the
 // phases right when items of forests with different nbuf share a CTA.
-template <int MODE>
+template <int MODE, bool D3>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
     constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
     const int R = p.R, F = p.F, C = p.C;
@@ -502,7 +493,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 if (lane == 0) base = atomicAdd(&sh.task_next[buf], 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= ntask) {  // the bin is claimed out: use the load in flight, then move on
-                    if (L.active) deep_finish<MODE>(p, xs, svotes, row0, L, w);
+                    if (L.active) deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
                     pop_tasks(p, ring, head, tail, L, lt_mask);
                     break;
                 }
@@ -575,7 +566,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 tail += __popc(pm);
                 __syncwarp();
             }
-            if (L.active) deep_finish<MODE>(p, xs, svotes, row0, L, w);
+            if (L.active) deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
             pop_tasks(p, ring, head, tail, L, lt_mask);
         }
         // this warp reads the bin's block no more; the last warp refills the buffer
@@ -596,7 +587,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         if (L.active) {
             uint32_t w[8];
             deep_issue(p, L, w);
-            deep_finish<MODE>(p, xs, svotes, row0, L, w);
+            deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
         }
     }
     __syncthreads();
@@ -673,14 +664,15 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 }
 
 // MINB = 1: one CTA of up to 1024 threads per SM (up to 64 registers a thread);
-// MINB = 3: up to three CTAs of up to 512 threads (at most 42 registers), for
-// launches whose shared memory leaves room for three CTAs.
-template <int MODE, int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 1024 : 512, MINB) fp_traverse_kernel(const TravParams p) {
+// MINB = 2: CTAs of up to 768 threads, at most 42 registers a thread, so that
+// two 24-warp or three 16-warp CTAs share an SM when shared memory allows:
+// more warps to hide the latency of the dependent loads of each walk.
+template <int MODE, int MINB, bool D3>
+__global__ void __launch_bounds__(MINB == 1 ? 1024 : 768, MINB) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE>(p, item, smem, sh);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE, D3>(p, item, smem, sh);
     cta_finish(sh);
 }
 
@@ -709,7 +701,10 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         if (item >= total) break;
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
-        run_item<FP_MODE_VOTES>(bp.p[j], item - bp.item_begin[j], smem, sh);
+        if (bp.p[j].deep3)  // forests of either kind share the launch
+            run_item<FP_MODE_VOTES, true>(bp.p[j], item - bp.item_begin[j], smem, sh);
+        else
+            run_item<FP_MODE_VOTES, false>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }

@@ -63,8 +63,8 @@ class Image:
         dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 4 * ne * g["n_super"]].view("<i4")
         self.deep_leaf = dl.reshape(-1, ne)
         if g["deep_levels"] == 3:
-            dk = img[g["off_deep_keys"]: g["off_deep_keys"] + 32 * g["n_super"]].view("<u4")
-            self.deep_keys = dk.reshape(-1, 8)
+            dk = img[g["off_deep_keys"]: g["off_deep_keys"] + 16 * g["n_super"]].view("<u4")
+            self.deep_keys = dk.reshape(-1, 4)  # full keys of slots 3..6
         self.ties = 0  # three levels: compares decided by the full keys in the last walk
         # forests with leaf values: a leaf reference names a slot of this table
         self.values = img[g["off_values"]: g["off_values"] + 4 * g["n_values"]].view("<f4")
@@ -168,33 +168,26 @@ class Image:
 
     def _step3(self, X, a, g_idx):
         """One three-level super-node per row of a: (exit, next reference or
-        LEAF, class or value slot).  Decides by the key prefixes, checks that
-        wherever the prefixes differ they agree with the full keys, and
-        counts the ties that the full keys decide."""
+        LEAF, class or value slot).  The first two levels compare full keys;
+        the last decides by its key prefix, checked wherever the prefixes
+        differ to agree with the full key; ties are counted."""
         g = self.h
         fb, cb = g["feature_bits"], g["class_bits"]
-        fm, s2 = (1 << fb) - 1, fb + 2 * cb
+        fm, s2 = (1 << fb) - 1, 2 * fb + 2 * cb
         w = self.sw[g_idx].astype(np.int64)
         K = self.deep_keys[g_idx].astype(np.int64)
         ar = np.arange(len(a))
-
-        def level(word, shift, full):
-            k = X[a, word & fm]
-            dp, tie = (k >> shift) > (word >> shift), (k >> shift) == (word >> shift)
-            return k > full, dp, tie
-
-        e0, p0, t0 = level(w[:, 0], fb, K[:, 0])
-        s1 = 1 + e0.astype(np.int64)
-        e1, p1, t1 = level(w[ar, s1], fb, K[ar, s1])
-        s2i = 3 + 2 * e0.astype(np.int64) + e1
-        e2, p2, t2 = level(w[ar, s2i], s2, K[ar, s2i])
-        # along the exact path, a prefix that differs from the observation's
-        # must decide as the full key does; the kernel's prefix walk follows
-        # this path up to its first tie, so it sees a tie exactly where this does
-        ok = (t0 | (p0 == e0)) & (t1 | (p1 == e1)) & (t2 | (p2 == e2))
-        assert np.all(ok), "a key prefix decided against the full key"
-        self.ties += int(np.sum(t0 | t1 | t2))
-        ex = 4 * e0.astype(np.int64) + 2 * e1.astype(np.int64) + e2.astype(np.int64)
+        e0 = X[a, (w[:, 3] >> fb) & fm] > w[:, 0]
+        n1 = np.where(e0, w[:, 2], w[:, 1])
+        e1 = X[a, (np.where(e0, w[:, 5], w[:, 4]) >> fb) & fm] > n1
+        j = 2 * e0.astype(np.int64) + e1.astype(np.int64)
+        n2 = w[ar, 3 + j]
+        k2 = X[a, n2 & fm]
+        e2 = k2 > K[ar, j]
+        p2, t2 = (k2 >> s2) > (n2 >> s2), (k2 >> s2) == (n2 >> s2)
+        assert np.all(t2 | (p2 == e2)), "a key prefix decided against the full key"
+        self.ties += int(np.sum(t2))
+        ex = 2 * j + e2.astype(np.int64)
         mask = w[:, 7] >> 24
         is_leaf = ((mask >> ex) & 1) == 1
         nref = g_idx.astype(np.int64) + (w[:, 7] & 0xFFFFFF) + _popc8(~mask & ((1 << ex) - 1))
@@ -202,5 +195,5 @@ class Image:
         if g["n_values"]:
             c3 = g["values3_base"] + 8 * g_idx.astype(np.int64) + ex
         else:
-            c3 = (w[ar, s2i] >> (fb + cb * e2.astype(np.int64))) & ((1 << cb) - 1)
+            c3 = (n2 >> (2 * fb + cb * e2.astype(np.int64))) & ((1 << cb) - 1)
         return ex, nref, c3.astype(np.int32)

@@ -81,6 +81,20 @@ def test_rows_on_thresholds(tiny_forest, tiny_rows, B, d, sel, dl):
     _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
 
 
+@pytest.mark.parametrize("rows_kind", ["sampled", "on_thresholds"])
+def test_short_key_prefixes(tiny_forest, tiny_rows, rows_kind):
+    """The tiny forest declared with 100 features: a 14-bit key prefix in the
+    last level of each three-level super-node, so ties are common and the
+    kernel decides them from the full keys."""
+    from edge_rows import rows_on_thresholds
+    f = datagen.Forest(100, tiny_forest.n_classes, tiny_forest.node_begin, tiny_forest.left, tiny_forest.right,
+                       tiny_forest.feature, tiny_forest.threshold, tiny_forest.leaf_class, tiny_forest.cardinality)
+    X = np.zeros((tiny_rows[0].shape[0], 100), np.float32)
+    X[:, :16] = tiny_rows[0] if rows_kind == "sampled" else rows_on_thresholds(tiny_forest, tiny_rows[0], seed=15)
+    for B, d, sel in [(4, 2, 1), (3, 1, 2), (2, 3, 3)]:
+        _check_all(f, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=3)
+
+
 @pytest.mark.parametrize("tile,warps", [(32, 1), (64, 3), (256, 8), (1024, 32)])
 def test_tiny_tiles_and_ragged_tail(tiny_forest, tiny_rows, tile, warps):
     X, _ = tiny_rows
@@ -182,10 +196,7 @@ def test_image_workload_params_grid():
     for B, d, sel, nb in [(128, 1, 3, 3), (16, 3, 3, 3), (8, 5, 3, 3), (1, 9, 3, 3), (16, 5, 1, 3), (1, 10, 1, 3),
                           (4, 7, 2, 3), (1, 11, 2, 2)]:
         _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, bin_buffers=nb)
-    # three-level super-nodes with 10 feature and 2 x 4 class bits: 14-bit key
-    # prefixes in the last level, so ties are frequent
-    for B, d, sel in [(16, 3, 2), (4, 6, 1)]:
-        _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=3)
+    # rows on the forest's thresholds, through its (two-level) super-nodes
     from edge_rows import rows_on_thresholds
     Xe = rows_on_thresholds(forest, X[:1000], seed=13)
-    _check_all(forest, Xe, None, bin_size=16, interleave_depth=3, head_select=2, deep_levels=3)
+    _check_all(forest, Xe, None, bin_size=16, interleave_depth=3, head_select=2)

@@ -169,8 +169,8 @@ def test_head_select_levels(tiny_forest, d):
                 assert ref == LEAF | int(tr["leaf_class"][v]) and par[e, k] == v
             else:
                 assert not ref & LEAF and par[e, k] == -1
-                root_key = im.deep_keys[ref, 0] if im.h["deep_levels"] == 3 else im.sthr[ref, 0]
-                assert root_key == thr_key(tr["threshold"][v]), "the exit roots the super-node of its node"
+                # the first word of either kind of super-node is its root's full key
+                assert im.sw[ref, 0] == thr_key(tr["threshold"][v]), "the exit roots the super-node of its node"
 
 
 def test_stat_order_in_super_nodes(tiny_forest):
@@ -316,6 +316,22 @@ def test_value_forest_records_decode_to_oracle(B, d, sel, dl):
     np.testing.assert_array_equal(im.values[slot], F.leaf_value[F.node_begin[:-1][None, :] + ref["leaf"]])
 
 
+def test_deep_levels_follow_field_widths():
+    """Three-level super-nodes hold two features and two classes beside the
+    last level's key prefix: by default they are used when those fields take
+    at most 16 bits, on request up to 24, and refused beyond."""
+    forest, _, _ = load("stump_split.txt")
+    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 3
+    forest.n_features, forest.n_classes = 784, 10  # 2 * 10 + 2 * 4 = 28 bits
+    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 2
+    with pytest.raises(fp.FPError) as ei:
+        fp.fp_pack_forest(forest, deep_levels=3)
+    assert ei.value.code == fp.FP_EUNSUPPORTED
+    forest.n_features, forest.n_classes = 100, 30  # 2 * 7 + 2 * 5 = 24 bits: on request only
+    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 2
+    assert fp.fp_pack_forest(forest, deep_levels=3).info()["deep_levels"] == 3
+
+
 def test_value_forest_rejects_non_finite_values():
     import datagen
     X, y = datagen.gen_regression(22, 500, 0, 1.0, 1.0)
@@ -365,11 +381,12 @@ def test_key_order_matches_float_compare():
 def test_three_level_super_nodes(tiny_forest):
     """Three-level super-nodes (format in fp_internal.h): seven slots holding
     the node, its children and grandchildren (a leaf carried down as
-    dummies), key prefixes and features in the words, full keys in the side
-    table, leaf mask, classes and leaf ids of the eight exits, and the
-    children side by side in exit order; a super-node whose children have
-    their own children expands the most frequently reached one first (Stat);
-    every internal node lies in the head or in exactly one super-node."""
+    dummies); full keys for the first two levels, features, key prefixes and
+    exit classes in the last level's words, its full keys in the side table;
+    leaf mask and leaf ids of the eight exits, and the children side by side
+    in exit order; a super-node whose children have their own children
+    expands the most frequently reached one first (Stat); every internal node
+    lies in the head or in exactly one super-node."""
     f = tiny_forest
     pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=1, head_select=1, deep_levels=3)
     im = Image(pk.image())
@@ -404,15 +421,18 @@ def test_three_level_super_nodes(tiny_forest):
             for i in range(3, 7):
                 u = sl[i]
                 ex += [u, u] if tr["left"][u] < 0 else [int(tr["left"][u]), int(tr["right"][u])]
+            sh = 2 * fb + 2 * cb
+            fm = (1 << fb) - 1
             for i, u in enumerate(sl):
-                sh = fb if i < 3 else fb + 2 * cb
-                if tr["left"][u] < 0:
-                    assert w[i] >> sh == 0 and im.deep_keys[g, i] == 0
-                    continue
-                covered += 1
-                key = int(thr_key(tr["threshold"][u]))
-                assert im.deep_keys[g, i] == key and w[i] >> sh == key >> sh
-                assert w[i] & ((1 << fb) - 1) == tr["feature"][u]
+                leaf = tr["left"][u] < 0
+                key = 0 if leaf else int(thr_key(tr["threshold"][u]))
+                feat = 0 if leaf else int(tr["feature"][u])
+                covered += not leaf
+                if i < 3:
+                    assert w[i] == key and (w[3 + i] >> fb) & fm == feat
+                else:
+                    assert im.deep_keys[g, i - 3] == key and w[i] >> sh == key >> sh and w[i] & fm == feat
+            assert (w[6] >> fb) & fm == 0
             mask = w[7] >> 24
             first = g + (w[7] & 0xFFFFFF)
             rank = 0
@@ -420,7 +440,7 @@ def test_three_level_super_nodes(tiny_forest):
             for e, c in enumerate(ex):
                 if tr["left"][c] < 0:
                     assert (mask >> e) & 1 and im.deep_leaf[g, e] == c
-                    assert (w[3 + e // 2] >> (fb + cb * (e & 1))) & ((1 << cb) - 1) == tr["leaf_class"][c]
+                    assert (w[3 + e // 2] >> (2 * fb + cb * (e & 1))) & ((1 << cb) - 1) == tr["leaf_class"][c]
                 else:
                     assert not (mask >> e) & 1 and im.deep_leaf[g, e] == -1
                     kids.append((first + rank, c))
@@ -433,3 +453,20 @@ def test_three_level_super_nodes(tiny_forest):
                 hot = max(firsts, key=lambda z: (int(tr["cardinality"][z[1]]), -z[0]))
                 assert hot[0] == min(fs for fs, _ in firsts)
     assert covered == pk.info()["n_internal"]
+
+
+def test_short_key_prefixes_decode_to_oracle_leaves(tiny_forest, tiny_rows):
+    """The tiny forest declared with 100 features: 7 feature bits twice and 2
+    class bits twice leave a 14-bit key prefix in the last level of each
+    three-level super-node, so many compares tie and the full keys decide."""
+    from edge_rows import rows_on_thresholds
+    f = datagen.Forest(100, tiny_forest.n_classes, tiny_forest.node_begin, tiny_forest.left, tiny_forest.right,
+                       tiny_forest.feature, tiny_forest.threshold, tiny_forest.leaf_class, tiny_forest.cardinality)
+    X = np.zeros((3000, 100), np.float32)
+    X[:, :16] = rows_on_thresholds(tiny_forest, tiny_rows[0][:3000], seed=14)
+    ref = oracle.predict(f, X)
+    im = Image(fp.fp_pack_forest(f, bin_size=4, interleave_depth=2, head_select=1, deep_levels=3).image())
+    assert im.h["feature_bits"] == 7
+    leaf, _ = im.walk(X)
+    np.testing.assert_array_equal(leaf, ref["leaf"])
+    assert im.ties > 300
