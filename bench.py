@@ -540,7 +540,7 @@ def run_batched(args, ws, rank, local):
     out = base_line(args, ws, value, total_ms,
                     {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
                      "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
-                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "launch")},
+                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "launch")},
                      "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
     out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
                 "e2e": None, "roofline": None, "cpu_baseline": None})

@@ -97,7 +97,8 @@ def _cache_path() -> str:
 
 def _time_predict(df, X, out, reps: int) -> float:
     """Milliseconds per call: classes (int32 out) or, for a forest with leaf
-    values, the value output (float32 out)."""
+    values, the value output (float32 out); at least `reps` calls, more for
+    short ones."""
     import torch
     if out.dtype == torch.float32:
         call = lambda: fp_predict_values(df, X, out, df.value_scale, df.value_bias)  # noqa: E731
@@ -106,6 +107,12 @@ def _time_predict(df, X, out, reps: int) -> float:
     call()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    call()
+    b.record()
+    torch.cuda.synchronize()
+    # short calls (small batches) are repeated until about 20 ms are timed
+    reps = max(reps, min(500, int(20.0 / max(a.elapsed_time(b), 1e-3))))
     a.record()
     for _ in range(reps):
         call()
@@ -205,7 +212,9 @@ def upload_tuned(forest, X, **kw):
     return df, best
 
 
-BATCHED_LAYOUTS = [(3, 9, 2), (8, 7, 2), (4, 8, 1), (16, 5, 2)]
+# (B, d, head_select[, deep_levels]): with two-level super-nodes for all, every
+# forest of the launch has the same kind of super-node
+BATCHED_LAYOUTS = [(3, 9, 2), (3, 9, 2, 2), (8, 7, 2), (8, 7, 2, 2), (4, 8, 1), (16, 5, 2)]
 BATCHED_LAUNCHES = [(0, 32, 16, 3), (0, 32, 32, 3)]
 
 
@@ -220,12 +229,14 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
     table, best, best_dfs = [], None, None
     votes = [torch.empty((x.shape[0], f.n_classes), dtype=torch.int32, device=x.device) for f, x in zip(forests, Xs)]
     cls = [torch.empty((x.shape[0],), dtype=torch.int32, device=x.device) for x in Xs]
-    for B, d, sel in (layouts or BATCHED_LAYOUTS):
+    for lay in (layouts or BATCHED_LAYOUTS):
+        B, d, sel = lay[:3]
+        dl = lay[3] if len(lay) > 3 else 0
         try:
-            dfs = [fp_upload(fp_pack_forest(f, bin_size=min(B, f.n_trees), interleave_depth=d, head_select=sel))
-                   for f in forests]
+            dfs = [fp_upload(fp_pack_forest(f, bin_size=min(B, f.n_trees), interleave_depth=d, head_select=sel,
+                                            deep_levels=dl)) for f in forests]
         except FPError as e:
-            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, error=str(e)))
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, error=str(e)))
             continue
         for launch in (launches or BATCHED_LAUNCHES):
             tile, warps, refill, nbuf = launch
@@ -233,7 +244,8 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
                 for df in dfs:
                     df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
             except FPError as e:
-                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, launch=launch, error=str(e)))
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, launch=launch,
+                                  error=str(e)))
                 continue
             fp_predict_batched(dfs, Xs, votes, cls)
             torch.cuda.synchronize()
@@ -243,7 +255,7 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
                 fp_predict_batched(dfs, Xs, votes, cls)
             b.record()
             torch.cuda.synchronize()
-            row = dict(bin_size=B, interleave_depth=d, head_select=sel, launch=list(launch),
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, launch=list(launch),
                        ms=a.elapsed_time(b) / reps)
             table.append(row)
             if best is None or row["ms"] < best["ms"]:

@@ -154,10 +154,11 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
         rc = configure<FP_MODE_VALUES>(&g, g.smem_values, &g.grid_values);
         if (rc) return rc;
     }
-    // the batched kernel may host any resident forest: allow it all of shared memory
-    cudaError_t e2 = cudaFuncSetAttribute(fp_traverse_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)budget);
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute(batched)");
+    // the batched kernels may host any resident forest: allow them all of shared memory
+    for (auto kern : {fp_traverse_batched_kernel<0>, fp_traverse_batched_kernel<2>, fp_traverse_batched_kernel<3>}) {
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute(batched)");
+    }
     f->R = g.R;
     f->threads = g.threads;
     f->refill = g.refill;
@@ -631,13 +632,17 @@ static int predict_batched_chunk(const fp_device_forest *const *forests, const f
         }
     }
     bp.work = reinterpret_cast<unsigned long long *>(sc);
+    // one walk compiled in when every forest has the same kind of super-node
+    int n3 = 0;
+    for (int32_t j = 0; j < m; ++j) n3 += bp.p[j].deep3 ? 1 : 0;
+    void (*kern)(BatchParams) = n3 == m ? fp_traverse_batched_kernel<3>
+                                : n3 == 0 ? fp_traverse_batched_kernel<2> : fp_traverse_batched_kernel<0>;
     int per_sm = 0, sms = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_traverse_batched_kernel, 32 * warps, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) {
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(bp.item_begin[m], (int64_t)per_sm * sms));
-        fp_traverse_batched_kernel<<<(unsigned)grid, 32 * warps, smem, s>>>(bp);
+        kern<<<(unsigned)grid, 32 * warps, smem, s>>>(bp);
         e = cudaGetLastError();
     }
     cudaFreeAsync(scratch, s);

@@ -24,7 +24,8 @@
 //   deep_leaf int32[4] (two-level) or [8] (three-level) per super-node: leaf
 //                                id behind each exit, or -1
 //
-// Thresholds are stored as order keys, not floats.  key(v) maps a float to a
+// In a forest with three-level super-nodes every threshold is stored as an
+// order key; otherwise thresholds are float bits.  key(v) maps a float to a
 // uint32 that orders like the float: +0 for -0, then the sign bit flipped for
 // v >= 0 and every bit flipped for v < 0; a NaN observation value maps to
 // 0xFFFFFFFF and a NaN threshold to 0.  For every observation value x and
@@ -79,8 +80,8 @@
 //
 // deep_levels = 2: a node v below the head together with its two children,
 // i.e. two levels of the tree resolved by one load:
-//   w[0] key of v's threshold      w[1] key of v's left child's threshold
-//   w[2] key of v's right child's threshold
+//   w[0] threshold of v (float)    w[1] threshold of v's left child
+//   w[2] threshold of v's right child
 //   w[3] features: v [9:0], left child [19:10], right child [29:20]
 //   w[4..7] exits: (left,left) (left,right) (right,left) (right,right)
 // A child that is a leaf keeps a dummy split and both of its exits name the

@@ -72,6 +72,15 @@ uint32_t thr_key(float t) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// A threshold as stored: its order key when the forest compares keys (with
+// three-level super-nodes), else its float bits.
+uint32_t thr_word(float t, bool keys) {
+    if (keys) return thr_key(t);
+    uint32_t u;
+    memcpy(&u, &t, 4);
+    return u;
+}
+
 // bits that hold the values 0 .. n-1 (at least 1)
 int32_t bits_for(int32_t n) {
     int32_t b = 1;
@@ -369,9 +378,9 @@ uint32_t ref_of(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base
 void encode_super(const TreeRef &t, const TreeLayout &lay, int32_t v, int64_t base, FpSuper &sn,
                   int32_t leaf_ids[4]) {
     const int32_t l = t.L[v], r = t.R[v];
-    sn.w[0] = thr_key(t.Th[v]);
-    sn.w[1] = t.leaf(l) ? 0u : thr_key(t.Th[l]);
-    sn.w[2] = t.leaf(r) ? 0u : thr_key(t.Th[r]);
+    sn.w[0] = thr_word(t.Th[v], false);
+    sn.w[1] = t.leaf(l) ? 0u : thr_word(t.Th[l], false);
+    sn.w[2] = t.leaf(r) ? 0u : thr_word(t.Th[r], false);
     const uint32_t fl = t.leaf(l) ? 0u : (uint32_t)t.Fe[l], fr = t.leaf(r) ? 0u : (uint32_t)t.Fe[r];
     sn.w[3] = (uint32_t)t.Fe[v] | (fl << 10) | (fr << 20);
     int32_t e[4];
@@ -664,7 +673,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                             uint32_t w[4] = {0, 0, 0, 0};
                             for (int c = 0; c < 3; ++c) {
                                 if (tr.leaf(vv[c])) continue;  // dummy: any outcome lands on the same leaf
-                                w[c] = thr_key(tr.Th[vv[c]]);
+                                w[c] = thr_word(tr.Th[vv[c]], three);
                                 w[3] |= (uint32_t)tr.Fe[vv[c]] << (10 * c);
                             }
                             memcpy(blk + (q * bn.stride + k) * 16, w, 16);
@@ -680,7 +689,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 if (select_levels) {
                     for (size_t s = 0; s < lay.slot.size(); ++s) {
                         const int32_t v = lay.slot[s];
-                        const uint32_t thr = tr.leaf(v) ? 0u : thr_key(tr.Th[v]);
+                        const uint32_t thr = tr.leaf(v) ? 0u : thr_word(tr.Th[v], three);
                         const uint32_t meta = tr.leaf(v) ? 0u : (uint32_t)tr.Fe[v] << 22;
                         uint8_t *rec = blk + ((int64_t)s * bn.stride + k) * 8;
                         memcpy(rec, &thr, 4);
@@ -703,7 +712,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                         tgt[0] = tgt[1] = (uint32_t)bn.nranks;
                         meta = 0;
                     } else {
-                        thr = thr_key(tr.Th[v]);
+                        thr = thr_word(tr.Th[v], three);
                         meta = (uint32_t)tr.Fe[v] << 22;
                         const int32_t c2[2] = {tr.L[v], tr.R[v]};
                         for (int s2 = 0; s2 < 2; ++s2) {

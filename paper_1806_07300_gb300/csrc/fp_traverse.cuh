@@ -8,9 +8,10 @@
 //   1. stages the tile's rows into shared memory feature-major
 //      (x[f * R + r]), so 32 lanes holding 32 consecutive rows read any
 //      features from 32 different banks (16-byte loads along a row when the
-//      feature count is a multiple of 4, else 4-byte cp.async), each value
-//      turned into its order key (fp_internal.h), so every compare below is
-//      an unsigned integer compare;
+//      feature count is a multiple of 4, else 4-byte cp.async); for a forest
+//      with three-level super-nodes each value is turned into its order key
+//      (fp_internal.h) and every compare is an unsigned integer compare,
+//      otherwise values and compares stay float;
 //   2. streams the bins' interleaved blocks (the heads of their trees,
 //      Section III-A Bin) through nbuf (2 or 3) shared-memory buffers with TMA bulk
 //      copies (cp.async.bulk) completing on mbarriers: a warp waits only for
@@ -147,6 +148,20 @@ __device__ __forceinline__ uint32_t obs_key(float v) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// A staged observation value: its order key (KEYS, forests with three-level
+// super-nodes) or its float bits.
+template <bool KEYS>
+__device__ __forceinline__ uint32_t staged(float v) {
+    return KEYS ? obs_key(v) : __float_as_uint(v);
+}
+
+// x <= t, the split's test (go left): keys compare as unsigned integers,
+// otherwise as floats (a NaN x or t goes right either way).
+template <bool KEYS>
+__device__ __forceinline__ bool goes_left(uint32_t x, uint32_t t) {
+    return KEYS ? x <= t : __uint_as_float(x) <= __uint_as_float(t);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -280,11 +295,11 @@ __device__ __forceinline__ void deep_finish(const TravParams &p, const uint32_t 
     }
     const int R = p.R;
     const uint32_t x0 = xs[(w[3] & 1023u) * R + L.r];
-    const uint32_t d0 = x0 <= w[0] ? 0u : 1u;
+    const uint32_t d0 = goes_left<false>(x0, w[0]) ? 0u : 1u;
     const uint32_t f1 = d0 ? (w[3] >> 20) & 1023u : (w[3] >> 10) & 1023u;
     const uint32_t t1 = d0 ? w[2] : w[1];
     const uint32_t x1 = xs[f1 * R + L.r];
-    const uint32_t d1 = x1 <= t1 ? 0u : 1u;
+    const uint32_t d1 = goes_left<false>(x1, t1) ? 0u : 1u;
     const uint32_t nref = d0 ? (d1 ? w[7] : w[6]) : (d1 ? w[5] : w[4]);
     if (nref & FP_REF_LEAF) {
         L.active = false;
@@ -345,7 +360,7 @@ template <int MODE, bool D3>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
     constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
     const int R = p.R, F = p.F, C = p.C;
-    uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // order keys of the tile's rows
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // the tile's rows: order keys (D3) or float bits
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
     const int nbuf = p.nbuf;
     uint8_t *const hbuf0 = smem + xs_bytes;  // nbuf bin-block buffers, head_smem bytes each
@@ -403,19 +418,19 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             uint32_t *d = dst + (4 * (q + u)) * R;
-                            d[0] = obs_key(v[u].x);
-                            d[R] = obs_key(v[u].y);
-                            d[2 * R] = obs_key(v[u].z);
-                            d[3 * R] = obs_key(v[u].w);
+                            d[0] = staged<D3>(v[u].x);
+                            d[R] = staged<D3>(v[u].y);
+                            d[2 * R] = staged<D3>(v[u].z);
+                            d[3 * R] = staged<D3>(v[u].w);
                         }
                     }
                     for (; q < nq; ++q) {
                         const float4 v = __ldg(rp + q);
                         uint32_t *d = dst + (4 * q) * R;
-                        d[0] = obs_key(v.x);
-                        d[R] = obs_key(v.y);
-                        d[2 * R] = obs_key(v.z);
-                        d[3 * R] = obs_key(v.w);
+                        d[0] = staged<D3>(v.x);
+                        d[R] = staged<D3>(v.y);
+                        d[2 * R] = staged<D3>(v.z);
+                        d[3 * R] = staged<D3>(v.w);
                     }
                 }
             }
@@ -436,7 +451,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     if (!LEAVES)
         for (int i = tid; i < rows * CS; i += blockDim.x) svotes[i] = 0;
     cp_async_wait_all();
-    if (!vec_rows) {  // each thread turns the values it copied into keys
+    if (D3 && !vec_rows) {  // each thread turns the values it copied into keys
         const int total = rows * F;
         for (int e = tid; e < total; e += blockDim.x) {
             const int r = e / F;
@@ -508,7 +523,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 const int r2 = my ? task - k2 * rows : 0;
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
-                const uint32_t *xr = xs + r2;  // this lane's row (keys)
+                const uint32_t *xr = xs + r2;  // this lane's row
                 if (p.levels == 2) {
                     // paired slots: a node and its two children per 16-byte record,
                     // successors 4q+1 .. 4q+4; (depth+1)/2 records per walk
@@ -516,10 +531,10 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     for (int l = 0; l <= p.depth; l += 2) {
                         const uint4 nd = hq[hr * stride];
                         const uint32_t x0 = xr[(nd.w & 1023u) * R];
-                        const uint32_t d0 = x0 <= nd.x ? 0u : 1u;
+                        const uint32_t d0 = goes_left<D3>(x0, nd.x) ? 0u : 1u;
                         const uint32_t f1 = d0 ? (nd.w >> 20) & 1023u : (nd.w >> 10) & 1023u;
                         const uint32_t x1 = xr[f1 * R];
-                        const uint32_t d1 = x1 <= (d0 ? nd.z : nd.y) ? 0u : 1u;
+                        const uint32_t d1 = goes_left<D3>(x1, d0 ? nd.z : nd.y) ? 0u : 1u;
                         hr = 4 * hr + 1 + 2 * d0 + d1;
                     }
                 } else if (p.levels) {
@@ -527,7 +542,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     for (int l = 0; l <= p.depth; ++l) {
                         const uint2 nd = hn[hr * stride];
                         const uint32_t xv = xr[(nd.y >> 22) * R];
-                        hr = 2 * hr + (xv <= nd.x ? 1u : 2u);
+                        hr = 2 * hr + (goes_left<D3>(xv, nd.x) ? 1u : 2u);
                     }
                 }
                 bool busy = my && !p.levels;
@@ -537,7 +552,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                         if (busy) {
                             const uint2 nd = hn[hr * stride];
                             const uint32_t m = nd.y;
-                            uint32_t nh = xr[(m >> 22) * R] <= nd.x
+                            uint32_t nh = goes_left<D3>(xr[(m >> 22) * R], nd.x)
                                               ? (m & FP_TARGET_MASK)
                                               : ((m >> FP_TARGET_BITS) & FP_TARGET_MASK);
                             busy = nh < (uint32_t)nranks;
@@ -688,6 +703,9 @@ struct BatchParams {
     unsigned long long *work;  // zeroed before the launch
 };
 
+// KIND: 2 or 3 when every forest of the launch has super-nodes of that many
+// levels (one walk compiled in), 0 for a mix (both, chosen per item).
+template <int KIND>
 __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
@@ -701,7 +719,7 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         if (item >= total) break;
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
-        if (bp.p[j].deep3)  // forests of either kind share the launch
+        if (KIND == 3 || (KIND == 0 && bp.p[j].deep3))
             run_item<FP_MODE_VOTES, true>(bp.p[j], item - bp.item_begin[j], smem, sh);
         else
             run_item<FP_MODE_VOTES, false>(bp.p[j], item - bp.item_begin[j], smem, sh);

@@ -58,7 +58,9 @@ class Image:
         self.tree_base = img[g["off_tree_base"]: g["off_tree_base"] + 4 * g["n_trees"]].view("<u4")
         deep = img[g["off_deep"]: g["off_deep"] + 32 * g["n_super"]]
         self.sw = deep.view("<u4").reshape(-1, 8)          # super-node words
-        self.sthr = self.sw[:, :3]                         # two levels: keys of v, left, right
+        self.sthr = deep.view("<f4").reshape(-1, 8)[:, :3]  # two levels: thresholds of v, left, right
+        # thresholds are order keys with three-level super-nodes, else floats
+        self.keys = g["deep_levels"] == 3
         ne = 8 if g["deep_levels"] == 3 else 4
         dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 4 * ne * g["n_super"]].view("<i4")
         self.deep_leaf = dl.reshape(-1, ne)
@@ -91,11 +93,16 @@ class Image:
         par = self.img[pb: pb + 4 * ne * st].view("<i4").reshape(ne, st)
         return thr, meta, exits, par
 
+    def word(self, t) -> np.ndarray:
+        """A threshold as the image stores it: its key, or its float bits."""
+        return thr_key(t) if self.keys else np.array(t, dtype=np.float32).view(np.uint32)
+
     def walk(self, X: np.ndarray):
         """Leaf id and class (or value slot) per (observation, tree), decoding
-        the records; X holds float observations, compared through their keys."""
+        the records; X holds float observations, compared through their keys
+        when the image stores keys."""
         g = self.h
-        X = obs_key(X).astype(np.int64)
+        X = obs_key(X).astype(np.int64) if self.keys else np.asarray(X, dtype=np.float32)
         self.ties = 0
         n, T = X.shape[0], g["n_trees"]
         leaf = np.full((n, T), -2, np.int32)
@@ -103,6 +110,8 @@ class Image:
         rows = np.arange(n)
         for b in range(g["n_bins"]):
             thr, meta, exits, par = self.head(b)
+            if not self.keys:
+                thr = thr.view(np.float32)
             bn = self.bins[b]
             for k in range(int(bn["width"])):
                 t = int(bn["first_tree"]) + k

@@ -165,11 +165,15 @@ def test_plain_baseline_fixture(name):
     np.testing.assert_array_equal(c.cpu().numpy(), exp["cls"])
 
 
-def test_batched_matches_single(tiny_forest, tiny_rows):
+@pytest.mark.parametrize("kinds", [(0, 0, 0, 0), (2, 2, 2, 2), (3, 2, 3, 2)])
+def test_batched_matches_single(tiny_forest, tiny_rows, kinds):
+    """One launch over four forests: all with three-level super-nodes (the
+    default here), all with two-level ones, or a mix of the two."""
     X, _ = tiny_rows
     forests, Xs, refs = [], [], []
     for i, n in enumerate([1, 700, 33, 5000]):
-        forests.append(fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=1 + 3 * i, interleave_depth=i)))
+        forests.append(fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=1 + 3 * i, interleave_depth=i,
+                                                      deep_levels=kinds[i])))
         Xs.append(_dev(X[i * 10: i * 10 + n]))
         refs.append(oracle.predict(tiny_forest, X[i * 10: i * 10 + n]))
     votes = [torch.empty((x.shape[0], tiny_forest.n_classes), dtype=torch.int32, device="cuda") for x in Xs]

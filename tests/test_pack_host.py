@@ -78,7 +78,7 @@ def _head_nodes(forest, t, im):
             continue
         v = rank_node[r]
         m = int(meta[r, k])
-        assert m >> 22 == tr["feature"][v] and thr[r, k] == thr_key(tr["threshold"][v])
+        assert m >> 22 == tr["feature"][v] and thr[r, k] == im.word(tr["threshold"][v])
         for c, tgt in ((int(tr["left"][v]), m & 2047), (int(tr["right"][v]), (m >> 11) & 2047)):
             if tgt < nr:
                 assert tr["left"][c] >= 0, "a head target is an internal node"
@@ -157,7 +157,7 @@ def test_head_select_levels(tiny_forest, d):
             v = slot[s]
             leaf = tr["left"][v] < 0
             if not leaf:
-                assert meta[s, k] >> 22 == tr["feature"][v] and thr[s, k] == thr_key(tr["threshold"][v])
+                assert meta[s, k] >> 22 == tr["feature"][v] and thr[s, k] == im.word(tr["threshold"][v])
                 assert meta[s, k] & ((1 << 22) - 1) == 0
             kids = (v, v) if leaf else (int(tr["left"][v]), int(tr["right"][v]))
             for q, c in enumerate(kids):
@@ -170,7 +170,7 @@ def test_head_select_levels(tiny_forest, d):
             else:
                 assert not ref & LEAF and par[e, k] == -1
                 # the first word of either kind of super-node is its root's full key
-                assert im.sw[ref, 0] == thr_key(tr["threshold"][v]), "the exit roots the super-node of its node"
+                assert im.sw[ref, 0] == im.word(tr["threshold"][v]), "the exit roots the super-node of its node"
 
 
 def test_stat_order_in_super_nodes(tiny_forest):
@@ -216,7 +216,7 @@ def test_head_interleaving_roots_contiguous(tiny_forest):
         for k in range(int(im.bins[b]["width"])):
             root = int(f.node_begin[first + k])
             assert meta[0, k] >> 22 == f.feature[root]
-            assert thr[0, k] == thr_key(f.threshold[root])
+            assert thr[0, k] == im.word(f.threshold[root])
 
 
 def test_pack_info_sizes(tiny_forest):
