@@ -234,6 +234,27 @@ int fp_predict_noalloc(const fp_device_forest *forest, const float *X, int64_t n
 int fp_predict_values(const fp_device_forest *forest, const float *X, int64_t n, float scale, float bias,
                       float *out, void *stream);
 
+/* fp_predict and fp_predict_values for rows and results in host memory: the
+ * rows go to the device in chunks of chunk_rows (0: a quarter of n, at least
+ * 65,536) through two device buffers; chunk c+1 is copied in on a copy
+ * stream the library keeps per device while chunk c is classified on
+ * `stream`, and each chunk's outputs are copied back on `stream` after its
+ * kernel.  Device memory for the buffers comes from the stream-ordered pool.
+ *   X_host          host, [n][n_features] FP32 row-major; page-locked memory
+ *                   (cudaHostAlloc, or a pinned torch tensor) lets the copies
+ *                   overlap the kernels, ordinary memory works but copies
+ *                   synchronously
+ *   out_votes_host  host, [n][n_classes] uint32, or NULL
+ *   out_class_host  host, [n] int32, or NULL
+ *   out_host        host, [n] float (fp_predict_values_host)
+ * The calls return once the work is queued; the results are in the host
+ * buffers, which must stay valid until then, when `stream` completes.
+ * Errors: as fp_predict / fp_predict_values. */
+int fp_predict_host(const fp_device_forest *forest, const float *X_host, int64_t n, uint32_t *out_votes_host,
+                    int32_t *out_class_host, int64_t chunk_rows, void *stream);
+int fp_predict_values_host(const fp_device_forest *forest, const float *X_host, int64_t n, float scale, float bias,
+                           float *out_host, int64_t chunk_rows, void *stream);
+
 /* Parity mode: the leaf each observation reaches in each tree.
  *   out_leaf   device, [n][n_trees] int32, tree-local node id of the leaf in
  *              the fp_forest_desc the forest was packed from

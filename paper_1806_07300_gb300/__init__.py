@@ -72,7 +72,7 @@ EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
            "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves", "fp_inject_fault", "fp_predict_values",
-           "fp_plain_predict_values"]
+           "fp_plain_predict_values", "fp_predict_host", "fp_predict_values_host"]
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +118,8 @@ def lib() -> ctypes.CDLL:
                 "fp_inject_fault": ([P, i32, i64], ctypes.c_int),
                 "fp_predict_values": ([P, P, i64, ctypes.c_float, ctypes.c_float, P, P], ctypes.c_int),
                 "fp_plain_predict_values": ([P, P, i64, i32, ctypes.c_float, ctypes.c_float, P, P], ctypes.c_int),
+                "fp_predict_host": ([P, P, i64, P, P, i64, P], ctypes.c_int),
+                "fp_predict_values_host": ([P, P, i64, ctypes.c_float, ctypes.c_float, P, i64, P], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -190,6 +192,33 @@ def _dptr(t, dtype, shape=None, name="tensor"):
     return t.data_ptr()
 
 
+def _hptr(t, dtype, shape=None, name="array"):
+    """Host pointer of a CPU torch tensor or numpy array after checking dtype,
+    contiguity and shape."""
+    if t is None:
+        return None
+    import numpy as np
+    import torch
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda:
+            raise TypeError(f"{name} must be in host memory")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        ok, ptr = t.is_contiguous(), t.data_ptr()
+    elif isinstance(t, np.ndarray):
+        want = {torch.float32: np.float32, torch.int32: np.int32}[dtype]
+        if t.dtype != want:
+            raise TypeError(f"{name} must be {np.dtype(want)}, got {t.dtype}")
+        ok, ptr = t.flags["C_CONTIGUOUS"], t.ctypes.data
+    else:
+        raise TypeError(f"{name} must be a CPU tensor or a numpy array")
+    if not ok:
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ptr
+
+
 # ------------------------------------------------------------ C-ABI mirrors
 
 def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_tile: int = 0,
@@ -229,6 +258,28 @@ def fp_predict_values(forest: "DeviceForest", X, out, scale: float, bias: float,
     xp = _dptr(X, _torch().float32, (n, forest.info["n_features"]), "X")
     op = _dptr(out, _torch().float32, (n,), "out")
     _check(lib().fp_predict_values(forest.handle, xp, n, scale, bias, op, _stream_ptr(stream)), "fp_predict_values")
+
+
+def fp_predict_host(forest: "DeviceForest", X_host, out_votes_host=None, out_class_host=None, chunk_rows: int = 0,
+                    stream=None) -> None:
+    """fp_predict for rows and results in host memory (pinned for overlap);
+    the results are there once `stream` completes."""
+    n = X_host.shape[0]
+    info = forest.info
+    xp = _hptr(X_host, _torch().float32, (n, info["n_features"]), "X_host")
+    vp = _hptr(out_votes_host, _torch().int32, (n, info["n_classes"]), "out_votes_host")
+    cp = _hptr(out_class_host, _torch().int32, (n,), "out_class_host")
+    _check(lib().fp_predict_host(forest.handle, xp, n, vp, cp, chunk_rows, _stream_ptr(stream)), "fp_predict_host")
+
+
+def fp_predict_values_host(forest: "DeviceForest", X_host, out_host, scale: float, bias: float, chunk_rows: int = 0,
+                           stream=None) -> None:
+    """fp_predict_values for rows and results in host memory."""
+    n = X_host.shape[0]
+    xp = _hptr(X_host, _torch().float32, (n, forest.info["n_features"]), "X_host")
+    op = _hptr(out_host, _torch().float32, (n,), "out_host")
+    _check(lib().fp_predict_values_host(forest.handle, xp, n, scale, bias, op, chunk_rows, _stream_ptr(stream)),
+           "fp_predict_values_host")
 
 
 def fp_predict_noalloc(forest: "DeviceForest", X, out_votes=None, out_class=None, stream=None) -> None:
@@ -362,6 +413,25 @@ class DeviceForest:
         fp_predict_values(self, X, out, self.value_scale if scale is None else scale,
                           self.value_bias if bias is None else bias, stream)
         return out
+
+    def predict_host(self, X_host, votes: bool = False, classes: bool = True, chunk_rows: int = 0, stream=None):
+        """Rows in host memory (a CPU tensor or numpy array; pinned tensors
+        let copies overlap the kernels) to host results: (votes, classes) as
+        pinned int32 tensors, or for a forest with leaf values the float32
+        outputs; waits for the stream."""
+        T = _torch()
+        n = X_host.shape[0]
+        s = stream if stream is not None else T.cuda.current_stream()
+        if self.value_scale is not None:  # a forest with leaf values
+            out = T.empty((n,), dtype=T.float32).pin_memory()
+            fp_predict_values_host(self, X_host, out, self.value_scale, self.value_bias, chunk_rows, s)
+            s.synchronize()
+            return out
+        v = T.empty((n, self.info["n_classes"]), dtype=T.int32).pin_memory() if votes else None
+        c = T.empty((n,), dtype=T.int32).pin_memory() if classes else None
+        fp_predict_host(self, X_host, v, c, chunk_rows, s)
+        s.synchronize()
+        return v, c
 
     def predict_leaves(self, X, stream=None):
         T = _torch()

@@ -675,3 +675,124 @@ extern "C" int fp_predict_batched(const fp_device_forest *const *forests, const 
     }
     return FP_OK;
 }
+
+// ------------------------------------------------- host buffers, pipelined
+
+namespace {
+
+std::mutex g_copy_mu;
+std::vector<cudaStream_t> g_copy_stream;  // per device, created on first use, kept for the process
+
+int copy_stream(int device, cudaStream_t *out) {
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    if ((int)g_copy_stream.size() <= device) g_copy_stream.resize((size_t)device + 1, nullptr);
+    if (!g_copy_stream[device]) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g_copy_stream[device], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_copy_stream[device] = nullptr;
+            return cuda_fail(e, "cudaStreamCreateWithFlags(copy)");
+        }
+    }
+    *out = g_copy_stream[device];
+    return FP_OK;
+}
+
+// Rows from host memory through the device in chunks: chunk c's rows are
+// copied in on the library's copy stream while chunk c-1 is classified on
+// the caller's stream, into one of two device buffers; each chunk's outputs
+// are copied back on the caller's stream after its kernel.  out_bytes: bytes
+// of output per row (one region per output); run(Xd, rows, outs) launches
+// the chunk's classification on `s`.
+template <class Run>
+int pipeline_host(const fp_device_forest *f, const float *X_host, int64_t n, int64_t chunk_rows,
+                  const int64_t out_bytes[2], void *const out_host[2], cudaStream_t s, const char *what, Run run) {
+    const int64_t F = f->hdr.n_features;
+    const int64_t chunk = std::min<int64_t>(n, chunk_rows > 0 ? chunk_rows : std::max<int64_t>(65536, (n + 3) / 4));
+    const int nbuf = n > chunk ? 2 : 1;
+    auto align = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
+    const int64_t in_b = align(chunk * F * 4), o0 = align(chunk * out_bytes[0]), o1 = align(chunk * out_bytes[1]);
+    const int64_t per_buf = in_b + o0 + o1;
+    cudaStream_t cs = nullptr;
+    int rc = copy_stream(f->device, &cs);
+    if (rc) return rc;
+    void *block = nullptr;
+    rc = scratch_alloc(f->device, &block, (size_t)(nbuf * per_buf), s);
+    if (rc) return rc;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // ready, in[2], free[2]
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);  // the block is allocated
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+    uint8_t *base = static_cast<uint8_t *>(block);
+    for (int64_t c = 0, r0 = 0; e == cudaSuccess && rc == FP_OK && r0 < n; ++c, r0 += chunk) {
+        const int b = (int)(c % nbuf);
+        const int64_t rows = std::min<int64_t>(chunk, n - r0);
+        uint8_t *buf = base + b * per_buf;
+        if (c >= nbuf) e = cudaStreamWaitEvent(cs, ev[3 + b], 0);  // chunk c-2 is done with the buffer
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf, X_host + r0 * F, (size_t)(rows * F * 4), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + b], 0);
+        if (e != cudaSuccess) break;
+        void *outs[2] = {out_host[0] ? buf + in_b : nullptr, out_host[1] ? buf + in_b + o0 : nullptr};
+        rc = run(reinterpret_cast<const float *>(buf), rows, outs);
+        for (int k = 0; k < 2 && rc == FP_OK && e == cudaSuccess; ++k)
+            if (out_host[k])
+                e = cudaMemcpyAsync(static_cast<uint8_t *>(out_host[k]) + r0 * out_bytes[k], outs[k],
+                                    (size_t)(rows * out_bytes[k]), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + b], s);
+    }
+    if (e != cudaSuccess || rc != FP_OK) cudaStreamSynchronize(cs);  // nothing of the copy stream outlives the block
+    cudaFreeAsync(block, s);
+    for (int i = 0; i < 5; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int fp_predict_host(const fp_device_forest *f, const float *X_host, int64_t n, uint32_t *out_votes_host,
+                               int32_t *out_class_host, int64_t chunk_rows, void *stream) {
+    if (!f || n < 0 || chunk_rows < 0 || (n > 0 && !X_host)) {
+        fp_set_error("fp_predict_host: bad arguments");
+        return FP_EINVAL;
+    }
+    if (f->hdr.n_values > 0) {
+        fp_set_error("fp_predict_host: the forest has leaf values; use fp_predict_values_host");
+        return FP_EINVAL;
+    }
+    if (n == 0 || (!out_votes_host && !out_class_host)) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t ob[2] = {4 * (int64_t)f->hdr.n_classes, 4};
+    void *const oh[2] = {out_votes_host, out_class_host};
+    return pipeline_host(f, X_host, n, chunk_rows, ob, oh, s, "fp_predict_host",
+                         [&](const float *Xd, int64_t rows, void *const outs[2]) {
+                             return fp_predict(f, Xd, rows, static_cast<uint32_t *>(outs[0]),
+                                               static_cast<int32_t *>(outs[1]), s);
+                         });
+}
+
+extern "C" int fp_predict_values_host(const fp_device_forest *f, const float *X_host, int64_t n, float scale,
+                                      float bias, float *out_host, int64_t chunk_rows, void *stream) {
+    if (!f || n < 0 || chunk_rows < 0 || (n > 0 && (!X_host || !out_host))) {
+        fp_set_error("fp_predict_values_host: bad arguments");
+        return FP_EINVAL;
+    }
+    if (f->hdr.n_values <= 0) {
+        fp_set_error("fp_predict_values_host: the forest was packed without leaf values");
+        return FP_EINVAL;
+    }
+    if (n == 0) return FP_OK;
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t ob[2] = {4, 0};
+    void *const oh[2] = {out_host, nullptr};
+    return pipeline_host(f, X_host, n, chunk_rows, ob, oh, s, "fp_predict_values_host",
+                         [&](const float *Xd, int64_t rows, void *const outs[2]) {
+                             return fp_predict_values(f, Xd, rows, scale, bias, static_cast<float *>(outs[0]), s);
+                         });
+}
