@@ -170,9 +170,11 @@ def measured_peaks():
 
 
 def kernel_fingerprint() -> str:
-    """Hash of the sources that decide the traversal kernel's memory traffic."""
+    """Hash of the sources that decide the traversal kernel's memory traffic:
+    the kernel, the image format and the packer (the launch parameters are
+    matched per captured entry)."""
     h = hashlib.sha1()
-    for name in ("fp_traverse.cuh", "fp_pack.cpp", "fp_internal.h", "fp_device.cu"):
+    for name in ("fp_traverse.cuh", "fp_pack.cpp", "fp_internal.h"):
         with open(os.path.join(ROOT, "paper_1806_07300_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
