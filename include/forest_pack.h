@@ -255,6 +255,57 @@ int fp_predict_host(const fp_device_forest *forest, const float *X_host, int64_t
 int fp_predict_values_host(const fp_device_forest *forest, const float *X_host, int64_t n, float scale, float bias,
                            float *out_host, int64_t chunk_rows, void *stream);
 
+/* ---- Serving: continuous batching over resident forests (library threads).
+ *
+ * A server owns `slots` CUDA streams with page-locked staging and device
+ * buffers on `device`, a batcher thread and a completion thread.  Requests
+ * (rows of one forest in host memory) are submitted from any thread; the
+ * batcher takes what has arrived, in arrival order up to max_rows rows (a
+ * larger request forms a launch of its own), groups it by forest and issues one
+ * fp_predict_batched launch on a free slot once the device reports at least
+ * the launch's bytes + mem_margin free (else it waits for launches in
+ * flight); with max_wait_s > 0 it first lets a batch grow until the oldest
+ * request has waited that long.  The completion thread polls launches in
+ * order (at most 60 s each, then FP_ETIMEOUT), copies each request's classes
+ * (and votes) into the caller's buffers and wakes its waiters.
+ *   fp_server_create        slots 1..64, max_rows >= 1, mem_margin >= 0 bytes;
+ *                           return_votes: requests may ask for votes
+ *   fp_server_add_forest    before fp_server_start; the forest must stay
+ *                           resident until fp_server_release; *out_id names it
+ *   fp_server_submit        X_host [n][n_features] FP32, out_class_host [n]
+ *                           int32 and/or out_votes_host [n][n_classes] uint32,
+ *                           all host, caller-owned, valid until the request
+ *                           is answered; *out: the request, library-owned
+ *                           until fp_request_release
+ *   fp_request_wait         waits up to timeout_s seconds (< 0: no limit);
+ *                           returns the request's status, or FP_ETIMEOUT if
+ *                           it is not answered yet
+ *   fp_request_latency      seconds from submit to answer, or -1 before
+ *   fp_request_release      waits for the answer, then frees the request
+ *   fp_server_stop          answers every queued request, then joins the
+ *                           threads; no submits afterwards
+ *   fp_server_stats         launches issued and admission waits so far
+ *   fp_server_set_free_bytes  tests: the free device bytes admission sees
+ *                           (-1: ask the device)
+ *   fp_server_release       stops if needed and frees the server
+ * Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA; a failed launch answers its
+ * requests with its status. */
+typedef struct fp_server fp_server;
+typedef struct fp_request fp_request;
+int fp_server_create(int32_t device, int32_t slots, int64_t max_rows, int64_t mem_margin, int32_t return_votes,
+                     double max_wait_s, fp_server **out);
+int fp_server_add_forest(fp_server *server, const fp_device_forest *forest, int32_t *out_id);
+int fp_server_start(fp_server *server);
+int fp_server_submit(fp_server *server, int32_t forest_id, const float *X_host, int64_t n, int32_t *out_class_host,
+                     uint32_t *out_votes_host, fp_request **out);
+int fp_request_wait(fp_request *request, double timeout_s);
+double fp_request_latency(const fp_request *request);
+void fp_request_release(fp_request *request);
+int fp_server_stop(fp_server *server);
+int fp_server_stats(const fp_server *server, int64_t *launches, int64_t *rejected_for_memory);
+int fp_server_set_free_bytes(fp_server *server, int64_t free_bytes);
+void fp_server_release(fp_server *server);
+
 /* Parity mode: the leaf each observation reaches in each tree.
  *   out_leaf   device, [n][n_trees] int32, tree-local node id of the leaf in
  *              the fp_forest_desc the forest was packed from

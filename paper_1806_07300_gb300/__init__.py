@@ -72,7 +72,10 @@ EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload
            "fp_predict_leaves", "fp_predict_batched", "fp_configure", "fp_predict_noalloc", "fp_sync_status", "fp_device_info_get", "fp_release_packed",
            "fp_release", "fp_last_error", "fp_plain_build", "fp_plain_predict", "fp_plain_bytes",
            "fp_plain_release", "fp_l2_read_probe", "fp_count_leaves", "fp_inject_fault", "fp_predict_values",
-           "fp_plain_predict_values", "fp_predict_host", "fp_predict_values_host"]
+           "fp_plain_predict_values", "fp_predict_host", "fp_predict_values_host", "fp_server_create",
+           "fp_server_add_forest", "fp_server_start", "fp_server_submit", "fp_request_wait", "fp_request_latency",
+           "fp_request_release", "fp_server_stop", "fp_server_stats", "fp_server_set_free_bytes",
+           "fp_server_release"]
 
 _lib = None
 _lock = threading.Lock()
@@ -120,6 +123,17 @@ def lib() -> ctypes.CDLL:
                 "fp_plain_predict_values": ([P, P, i64, i32, ctypes.c_float, ctypes.c_float, P, P], ctypes.c_int),
                 "fp_predict_host": ([P, P, i64, P, P, i64, P], ctypes.c_int),
                 "fp_predict_values_host": ([P, P, i64, ctypes.c_float, ctypes.c_float, P, i64, P], ctypes.c_int),
+                "fp_server_create": ([i32, i32, i64, i64, i32, ctypes.c_double, ctypes.POINTER(P)], ctypes.c_int),
+                "fp_server_add_forest": ([P, P, ctypes.POINTER(i32)], ctypes.c_int),
+                "fp_server_start": ([P], ctypes.c_int),
+                "fp_server_submit": ([P, i32, P, i64, P, P, ctypes.POINTER(P)], ctypes.c_int),
+                "fp_request_wait": ([P, ctypes.c_double], ctypes.c_int),
+                "fp_request_latency": ([P], ctypes.c_double),
+                "fp_request_release": ([P], None),
+                "fp_server_stop": ([P], ctypes.c_int),
+                "fp_server_stats": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+                "fp_server_set_free_bytes": ([P, i64], ctypes.c_int),
+                "fp_server_release": ([P], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)

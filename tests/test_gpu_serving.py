@@ -50,6 +50,33 @@ def _requests(rows, n, seed):
     return out
 
 
+def test_requests_past_stop_and_errors(served):
+    """stop() answers every queued request; a wrong forest name or a submit
+    after stop is refused; a request larger than max_rows is launched alone."""
+    forests, rows = served
+    srv = _server(forests, slots=2, max_rows=1000)
+    srv.start()
+    hs = [srv.submit("tiny", rows["tiny"][i * 50: i * 50 + 50]) for i in range(40)]
+    srv.stop()
+    for i, h in enumerate(hs):
+        assert h.wait(0) and h.error is None and h.latency_s > 0
+        np.testing.assert_array_equal(h.classes, oracle.predict(forests["tiny"], rows["tiny"][i * 50: i * 50 + 50],
+                                                                leaves=False)["cls"])
+    import paper_1806_07300_gb300 as fp
+    with pytest.raises(fp.FPError):
+        srv.submit("tiny", rows["tiny"][:10])
+    with pytest.raises(KeyError):
+        srv.submit("nope", rows["tiny"][:10])
+    srv.close()
+    srv2 = _server(forests, slots=1, max_rows=100).start()
+    big = srv2.submit("tiny", rows["tiny"][:1001])
+    small = srv2.submit("tiny", rows["tiny"][:7])
+    assert big.wait(60) and small.wait(60) and big.error is None and small.error is None
+    np.testing.assert_array_equal(big.classes, oracle.predict(forests["tiny"], rows["tiny"][:1001], leaves=False)["cls"])
+    assert srv2.launches == 2
+    srv2.close()
+
+
 def test_mix_equals_alone_and_oracle(served):
     forests, rows = served
     reqs = _requests(rows, 300, seed=3)
@@ -88,16 +115,8 @@ def test_admission_waits_for_memory(served):
     flight to finish instead of starting; every request still completes."""
     forests, rows = served
     reqs = _requests(rows, 60, seed=5)
-    srv = _server(forests, slots=2, max_rows=2000)
-    real = torch.cuda.mem_get_info
-    calls = {"n": 0}
-
-    def tight(device=None):
-        calls["n"] += 1
-        free, total = real(device)
-        return (srv.mem_margin - 1, total) if calls["n"] % 2 else (free, total)
-
-    srv._admit_info = tight
+    srv = _server(forests, slots=2, max_rows=1000)
+    srv.set_free_bytes(srv.mem_margin - 1)  # never enough: each launch waits until none is in flight
     with srv:
         hs = [srv.submit(*r) for r in reqs]
         for h in hs:
