@@ -491,6 +491,9 @@ def run_packed(args, ws, rank, local):
         "packed_vs_plain": (value / ws / plain["value"]) if plain else None,
         "e2e": e2e,
         "gpu_launches": args.steps,
+        # per-launch CUDA-event times of the timed steps: median and spread
+        "launch_ms": {"median": statistics.median(per_launch_ms), "min": min(per_launch_ms),
+                      "max": max(per_launch_ms), "n": len(per_launch_ms)},
         "roofline": roofline,
         "cpu_baseline": {"value": cpu_value, "unit": "observations/s", "cores": threads, "kind": "oracle",
                          "sample": f"first {m} of {n} rows ({cpu_s:.1f} s)",
