@@ -10,12 +10,23 @@
  *     of its bin into one contiguous block (Section III-A, Bin layout; d = 0
  *     interleaves the roots only, Fig. 2), staged into shared memory;
  *   - deeper nodes are laid out per tree depth-first with the more frequently
- *     reached child placed next to its parent (Section III-A, Stat), in
- *     super-nodes of two levels that fill one 32-byte memory sector;
+ *     reached child placed next to or first after its parent (Section III-A,
+ *     Stat), in super-nodes of two or three tree levels that fill one 32-byte
+ *     memory sector (three levels store thresholds as order-preserving keys,
+ *     the last level's shortened, with exact tie-breaking from a side table);
  *   - leaves are not stored as nodes: their class is folded into the reference
  *     that leads to them (Section III-A, DF-, which replaces leaves with
  *     per-class nodes);
  * and reduces the per-tree leaf classes to a majority vote.
+ *
+ * Groups of entry points: packing and upload (fp_pack_forest, fp_upload,
+ * fp_configure); classification of device rows (fp_predict,
+ * fp_predict_values, fp_predict_leaves, fp_predict_batched,
+ * fp_predict_noalloc); classification of host rows with copies pipelined
+ * against the kernels (fp_predict_host, fp_predict_values_host); the serving
+ * runtime (fp_server_*, fp_request_*); the plain-layout baseline
+ * (fp_plain_*); statistics and probes (fp_count_leaves, fp_l2_read_probe);
+ * status and fault injection (fp_sync_status, fp_inject_fault).
  *
  * Conventions for every entry point:
  *   - Return FP_OK (0) or a negative FP_E* code; no C++ exception crosses the
