@@ -116,3 +116,18 @@ def test_host_errors(tiny_forest, tiny_df):
     with pytest.raises(TypeError):
         fp.fp_predict_host(tiny_df, torch.zeros((4, tiny_forest.n_features), device="cuda"), None, cls)
     fp.fp_predict_host(tiny_df, np.zeros((0, tiny_forest.n_features), np.float32), None, np.zeros(0, np.int32))
+
+
+def test_host_allocation_failure_then_recovery(tiny_forest, tiny_rows, tiny_df):
+    """An injected failure of the pipeline's device allocation returns
+    FP_ENOMEM and leaves nothing behind; the next call classifies correctly."""
+    X = torch.from_numpy(np.ascontiguousarray(tiny_rows[0][:3000])).pin_memory()
+    cls = torch.empty((3000,), dtype=torch.int32).pin_memory()
+    s = torch.cuda.current_stream()
+    fp.fp_inject_fault(tiny_df, fp.FP_FAULT_ALLOC, 1)
+    with pytest.raises(fp.FPError) as e:
+        fp.fp_predict_host(tiny_df, X, None, cls, 1000, s)
+    assert e.value.code == fp.FP_ENOMEM
+    fp.fp_predict_host(tiny_df, X, None, cls, 1000, s)
+    s.synchronize()
+    np.testing.assert_array_equal(cls.numpy(), oracle.predict(tiny_forest, X.numpy())["cls"])

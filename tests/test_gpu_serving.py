@@ -124,3 +124,20 @@ def test_admission_waits_for_memory(served):
     assert srv.rejected_for_memory > 0
     for (name, X), h in zip(reqs, hs):
         np.testing.assert_array_equal(h.classes, oracle.predict(forests[name], X, leaves=False)["cls"])
+
+
+def test_failed_launch_answers_its_requests(served):
+    """A launch whose scratch allocation fails (injected on the host) answers
+    its requests with FP_ENOMEM; the server keeps serving the next ones."""
+    import paper_1806_07300_gb300 as fp
+    forests, rows = served
+    with _server(forests, slots=1) as srv:
+        first = srv.submit("tiny", rows["tiny"][:40])
+        assert first.wait(60) and first.error is None
+        fp.fp_inject_fault(srv.forests["tiny"].df, fp.FP_FAULT_ALLOC, 1)
+        bad = srv.submit("tiny", rows["tiny"][:40])
+        assert bad.wait(60) and bad.error == "FP_ENOMEM"
+        good = srv.submit("tiny", rows["tiny"][40:90])
+        assert good.wait(60) and good.error is None
+        np.testing.assert_array_equal(good.classes, oracle.predict(forests["tiny"], rows["tiny"][40:90],
+                                                                   leaves=False)["cls"])
