@@ -180,10 +180,10 @@ def kernel_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, params: dict, rows: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to `rows`
-    (traffic grows with the rows swept), or None when the kernel changed
-    since the counters were taken or these parameters were not captured."""
+def profiled_entry(workload: str, params: dict):
+    """The committed ncu counters of one launch for these parameters, or None
+    when the kernel changed since they were taken or the parameters were not
+    captured."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(path):
         return None
@@ -193,8 +193,15 @@ def profiled_traffic(workload: str, params: dict, rows: int):
         return None
     for e in d.get("entries", []):  # one per captured launch configuration
         if e["params"] == params:
-            return e["dram_bytes_per_launch"] * rows / e["rows"]
+            return e
     return None
+
+
+def profiled_traffic(workload: str, params: dict, rows: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `rows`
+    (traffic grows with the rows swept), or None (see profiled_entry)."""
+    e = profiled_entry(workload, params)
+    return None if e is None else e["dram_bytes_per_launch"] * rows / e["rows"]
 
 
 def cpu_sample(forest, X, target_s: float, threads: int):
@@ -457,6 +464,15 @@ def run_packed(args, ws, rank, local):
     params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "obs_tile",
                                    "warps_per_cta", "refill_lanes", "bin_buffers")}
     traffic = profiled_traffic(name, params, n)
+    # the sector-granular figure: 32 B per global-load sector the kernel touched
+    # (ncu, same launch configuration), the practical bound beside the
+    # algorithmic 8 B per node visit
+    pe = profiled_entry(name, params)
+    sectors = None
+    if pe is not None and pe.get("global_load_sectors"):
+        sectors = {"bytes_per_obs": 32.0 * pe["global_load_sectors"] / pe["rows"],
+                   "sectors_per_request": pe["global_load_sectors"] / pe["global_load_requests"],
+                   "source": "ncu l1tex__t_sectors / l1tex__t_requests_pipe_lsu_mem_global_op_ld, one launch"}
     kernel = "fp_traverse_kernel<values>" if values else "fp_traverse_kernel<votes>"
     visits_per_s = visits_per_obs * n / (avg_launch_ms / 1e3)
     if info["n_super"] == 0:
@@ -479,7 +495,10 @@ def run_packed(args, ws, rank, local):
                     "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
                     "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s,
                     "l2": {"peak": l2_gbs, "achieved": achieved, "frac": achieved / l2_gbs, "unit": "GB/s",
-                           "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"}}
+                           "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"},
+                    "sector_granular": None if sectors is None else dict(
+                        sectors, achieved_gbs=sectors["bytes_per_obs"] * n / (avg_launch_ms / 1e3) / 1e9,
+                        frac_of_l2=sectors["bytes_per_obs"] * n / (avg_launch_ms / 1e3) / 1e9 / l2_gbs)}
     out = base_line(args, ws, value, total_ms,
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
                      "n_classes": C, **params, "passes": info["passes"], "forest_bytes": info["total_bytes"],
