@@ -91,12 +91,25 @@ size_t smem_bytes(int R, int F, int head_smem, int nbuf, int C, int warps, bool 
 
 // The kernel variant for a forest and block size: its kind of super-node
 // (two or three levels), and up to 768 threads run the build for several CTAs
-// per SM (<= 42 registers), larger blocks the one-CTA build.
+// per SM (<= 42 registers), larger blocks the one-CTA build ...
+template <int MODE, bool D3, int HK>
+void (*traverse_kernel_sized(const fp_device_forest *f))(TravParams) {
+    return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, D3, HK> : fp_traverse_kernel<MODE, 1, D3, HK>;
+}
+
+// ... and its head kind (compiled in: 0 ranked, 1 level slots, 2 paired).
+template <int MODE, bool D3>
+void (*traverse_kernel_deep(const fp_device_forest *f))(TravParams) {
+    switch (f->hdr.head_select) {
+        case 1: return traverse_kernel_sized<MODE, D3, 1>(f);
+        case 2: return traverse_kernel_sized<MODE, D3, 2>(f);
+        default: return traverse_kernel_sized<MODE, D3, 0>(f);
+    }
+}
+
 template <int MODE>
 void (*traverse_kernel(const fp_device_forest *f))(TravParams) {
-    if (f->hdr.deep_levels == 3)
-        return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, true> : fp_traverse_kernel<MODE, 1, true>;
-    return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, false> : fp_traverse_kernel<MODE, 1, false>;
+    return f->hdr.deep_levels == 3 ? traverse_kernel_deep<MODE, true>(f) : traverse_kernel_deep<MODE, false>(f);
 }
 
 template <int MODE>

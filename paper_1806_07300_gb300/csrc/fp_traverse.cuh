@@ -356,9 +356,13 @@ __device__ __forceinline__ void cta_finish(CtaShared &sh) {
 // completes its barrier's phase k, so a wait needs the buffer's copy count
 // at the item's start (use0) plus bi / nbuf.  Counting per buffer keeps the
 // phases right when items of forests with different nbuf share a CTA.
-template <int MODE, bool D3>
+// HK: the head kind when known at compile time (0 ranked, 1 level slots,
+// 2 paired level slots), or -1 to read it from p.levels (the batched kernel,
+// whose forests may differ).
+template <int MODE, bool D3, int HK>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
     constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
+    const int levels = HK >= 0 ? HK : p.levels;
     const int R = p.R, F = p.F, C = p.C;
     uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // the tile's rows: order keys (D3) or float bits
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
@@ -497,7 +501,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         const uint8_t *blk = hbuf0 + buf * p.head_smem;
         const uint2 *hnode = reinterpret_cast<const uint2 *>(blk);
         const uint32_t *hexit =
-            reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * (p.levels == 2 ? 16 : 8));
+            reinterpret_cast<const uint32_t *>(blk + (size_t)nranks * stride * (levels == 2 ? 16 : 8));
 
         for (;;) {
             uint32_t w[8];
@@ -524,10 +528,11 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
                 const uint32_t *xr = xs + r2;  // this lane's row
-                if (p.levels == 2) {
+                if (levels == 2) {
                     // paired slots: a node and its two children per 16-byte record,
                     // successors 4q+1 .. 4q+4; (depth+1)/2 records per walk
                     const uint4 *hq = reinterpret_cast<const uint4 *>(blk) + k2;
+#pragma unroll 3
                     for (int l = 0; l <= p.depth; l += 2) {
                         const uint4 nd = hq[hr * stride];
                         const uint32_t x0 = xr[(nd.w & 1023u) * R];
@@ -537,15 +542,16 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                         const uint32_t d1 = goes_left<D3>(x1, d0 ? nd.z : nd.y) ? 0u : 1u;
                         hr = 4 * hr + 1 + 2 * d0 + d1;
                     }
-                } else if (p.levels) {
+                } else if (levels) {
                     // implicit slots: every walk takes depth+1 steps, children 2s+1, 2s+2
+#pragma unroll 3
                     for (int l = 0; l <= p.depth; ++l) {
                         const uint2 nd = hn[hr * stride];
                         const uint32_t xv = xr[(nd.y >> 22) * R];
                         hr = 2 * hr + (goes_left<D3>(xv, nd.x) ? 1u : 2u);
                     }
                 }
-                bool busy = my && !p.levels;
+                bool busy = my && !levels;
                 while (__any_sync(0xffffffffu, busy)) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {  // two steps per vote
@@ -682,12 +688,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 // MINB = 2: CTAs of up to 768 threads, at most 42 registers a thread, so that
 // two 24-warp or three 16-warp CTAs share an SM when shared memory allows:
 // more warps to hide the latency of the dependent loads of each walk.
-template <int MODE, int MINB, bool D3>
+template <int MODE, int MINB, bool D3, int HK>
 __global__ void __launch_bounds__(MINB == 1 ? 1024 : 768, MINB) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE, D3>(p, item, smem, sh);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE, D3, HK>(p, item, smem, sh);
     cta_finish(sh);
 }
 
@@ -720,9 +726,9 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
         if (KIND == 3 || (KIND == 0 && bp.p[j].deep3))
-            run_item<FP_MODE_VOTES, true>(bp.p[j], item - bp.item_begin[j], smem, sh);
+            run_item<FP_MODE_VOTES, true, -1>(bp.p[j], item - bp.item_begin[j], smem, sh);
         else
-            run_item<FP_MODE_VOTES, false>(bp.p[j], item - bp.item_begin[j], smem, sh);
+            run_item<FP_MODE_VOTES, false, -1>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }
