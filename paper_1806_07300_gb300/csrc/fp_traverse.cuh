@@ -532,7 +532,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     // paired slots: a node and its two children per 16-byte record,
                     // successors 4q+1 .. 4q+4; (depth+1)/2 records per walk
                     const uint4 *hq = reinterpret_cast<const uint4 *>(blk) + k2;
-#pragma unroll 3
+#pragma unroll 1  // measured: unrolling the head walk only adds instructions
                     for (int l = 0; l <= p.depth; l += 2) {
                         const uint4 nd = hq[hr * stride];
                         const uint32_t x0 = xr[(nd.w & 1023u) * R];
@@ -544,7 +544,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     }
                 } else if (levels) {
                     // implicit slots: every walk takes depth+1 steps, children 2s+1, 2s+2
-#pragma unroll 3
+#pragma unroll 1
                     for (int l = 0; l <= p.depth; ++l) {
                         const uint2 nd = hn[hr * stride];
                         const uint32_t xv = xr[(nd.y >> 22) * R];
