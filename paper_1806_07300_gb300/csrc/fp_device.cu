@@ -112,6 +112,33 @@ void (*traverse_kernel(const fp_device_forest *f))(TravParams) {
     return f->hdr.deep_levels == 3 ? traverse_kernel_deep<MODE, true>(f) : traverse_kernel_deep<MODE, false>(f);
 }
 
+// Every instance of the batched kernel: super-node kind (0 mixed, 2, 3) x
+// head kind (-1 mixed, 0 ranked, 1, 2).
+template <int KIND>
+void add_batched(std::vector<void (*)(BatchParams)> &v) {
+    v.push_back(fp_traverse_batched_kernel<KIND, -1>);
+    v.push_back(fp_traverse_batched_kernel<KIND, 0>);
+    v.push_back(fp_traverse_batched_kernel<KIND, 1>);
+    v.push_back(fp_traverse_batched_kernel<KIND, 2>);
+}
+
+const std::vector<void (*)(BatchParams)> &batched_kernels() {
+    static const std::vector<void (*)(BatchParams)> v = [] {
+        std::vector<void (*)(BatchParams)> k;
+        add_batched<0>(k);
+        add_batched<2>(k);
+        add_batched<3>(k);
+        return k;
+    }();
+    return v;
+}
+
+// The instance for a launch: index 4 * kind + (head kind + 1) into batched_kernels().
+void (*batched_kernel(int kind, int hk))(BatchParams) {
+    const int ki = kind == 3 ? 2 : (kind == 2 ? 1 : 0);
+    return batched_kernels()[(size_t)(4 * ki + (hk + 1))];
+}
+
 template <int MODE>
 int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
     auto kern = traverse_kernel<MODE>(f);
@@ -168,7 +195,7 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
         if (rc) return rc;
     }
     // the batched kernels may host any resident forest: allow them all of shared memory
-    for (auto kern : {fp_traverse_batched_kernel<0>, fp_traverse_batched_kernel<2>, fp_traverse_batched_kernel<3>}) {
+    for (auto kern : batched_kernels()) {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
         if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute(batched)");
     }
@@ -645,11 +672,14 @@ static int predict_batched_chunk(const fp_device_forest *const *forests, const f
         }
     }
     bp.work = reinterpret_cast<unsigned long long *>(sc);
-    // one walk compiled in when every forest has the same kind of super-node
-    int n3 = 0;
-    for (int32_t j = 0; j < m; ++j) n3 += bp.p[j].deep3 ? 1 : 0;
-    void (*kern)(BatchParams) = n3 == m ? fp_traverse_batched_kernel<3>
-                                : n3 == 0 ? fp_traverse_batched_kernel<2> : fp_traverse_batched_kernel<0>;
+    // one walk compiled in when every forest has the same kind of super-node,
+    // and the head kind when every forest has the same one
+    int n3 = 0, hk = bp.p[0].levels;
+    for (int32_t j = 0; j < m; ++j) {
+        n3 += bp.p[j].deep3 ? 1 : 0;
+        if (bp.p[j].levels != hk) hk = -1;
+    }
+    void (*kern)(BatchParams) = batched_kernel(n3 == m ? 3 : (n3 == 0 ? 2 : 0), hk);
     int per_sm = 0, sms = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);

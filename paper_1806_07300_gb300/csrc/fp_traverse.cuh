@@ -710,8 +710,9 @@ struct BatchParams {
 };
 
 // KIND: 2 or 3 when every forest of the launch has super-nodes of that many
-// levels (one walk compiled in), 0 for a mix (both, chosen per item).
-template <int KIND>
+// levels (one walk compiled in), 0 for a mix (both, chosen per item).  HK:
+// the head kind when all forests share it (0 ranked, 1, 2), else -1.
+template <int KIND, int HK>
 __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
@@ -726,9 +727,9 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
         if (KIND == 3 || (KIND == 0 && bp.p[j].deep3))
-            run_item<FP_MODE_VOTES, true, -1>(bp.p[j], item - bp.item_begin[j], smem, sh);
+            run_item<FP_MODE_VOTES, true, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
         else
-            run_item<FP_MODE_VOTES, false, -1>(bp.p[j], item - bp.item_begin[j], smem, sh);
+            run_item<FP_MODE_VOTES, false, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }
