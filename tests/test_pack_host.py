@@ -295,6 +295,24 @@ def test_null_arguments_rejected():
     L.fp_release(None)
     L.fp_release_packed(None)
     L.fp_plain_release(None)
+    # host-buffer calls and the serving runtime check their arguments before any CUDA call
+    assert L.fp_predict_host(None, None, 0, None, None, 0, None) == fp.FP_EINVAL
+    assert L.fp_predict_values_host(None, None, 0, 1.0, 0.0, None, 0, None) == fp.FP_EINVAL
+    out = ctypes.c_void_p()
+    assert L.fp_server_create(0, 0, 1024, 0, 0, 0.0, ctypes.byref(out)) == fp.FP_EINVAL   # no slot
+    assert L.fp_server_create(0, 2, 0, 0, 0, 0.0, ctypes.byref(out)) == fp.FP_EINVAL     # no rows
+    assert L.fp_server_create(0, 2, 1024, -1, 0, 0.0, ctypes.byref(out)) == fp.FP_EINVAL  # negative margin
+    assert L.fp_server_create(0, 2, 1024, 0, 0, 0.0, None) == fp.FP_EINVAL
+    assert L.fp_server_add_forest(None, None, None) == fp.FP_EINVAL
+    assert L.fp_server_start(None) == fp.FP_EINVAL
+    assert L.fp_server_submit(None, 0, None, 1, None, None, ctypes.byref(out)) == fp.FP_EINVAL
+    assert L.fp_request_wait(None, 0.0) == fp.FP_EINVAL
+    assert L.fp_request_latency(None) == -1.0
+    assert L.fp_server_stop(None) == fp.FP_EINVAL
+    assert L.fp_server_stats(None, None, None) == fp.FP_EINVAL
+    assert L.fp_server_set_free_bytes(None, 0) == fp.FP_EINVAL
+    L.fp_request_release(None)
+    L.fp_server_release(None)
 
 
 @pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 3), (3, 6, 3), (2, 9, 1), (3, 9, 0)])
