@@ -61,3 +61,26 @@ def test_reference_arm_under_torchrun(tmp_path):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_profiled_traffic_lookup(tmp_path, monkeypatch):
+    """bench.py takes DRAM traffic and sector counts from a committed capture
+    only when the kernel sources still hash to the capture's fingerprint and
+    the launch parameters match an entry exactly; it scales traffic by rows."""
+    sys.path.insert(0, ROOT)
+    import bench
+    params = {"bin_size": 4, "interleave_depth": 9, "head_select": 2, "deep_levels": 3, "obs_tile": 992,
+              "warps_per_cta": 32, "refill_lanes": 16, "bin_buffers": 2}
+    (tmp_path / "profiles").mkdir()
+    rec = {"fingerprint": bench.kernel_fingerprint(),
+           "entries": [{"params": params, "rows": 1000, "dram_bytes_per_launch": 5000,
+                        "global_load_sectors": 300, "global_load_requests": 12}]}
+    (tmp_path / "profiles" / "traffic_hbm.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_fingerprint", lambda: rec["fingerprint"])
+    assert bench.profiled_traffic("hbm", params, 4000) == 20000
+    assert bench.profiled_entry("hbm", params)["global_load_sectors"] == 300
+    assert bench.profiled_traffic("hbm", dict(params, refill_lanes=24), 4000) is None
+    assert bench.profiled_traffic("image", params, 4000) is None
+    monkeypatch.setattr(bench, "kernel_fingerprint", lambda: "0000000000000000")
+    assert bench.profiled_traffic("hbm", params, 4000) is None
