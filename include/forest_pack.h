@@ -25,7 +25,8 @@
  * fp_predict_noalloc); classification of host rows with copies pipelined
  * against the kernels (fp_predict_host, fp_predict_values_host); the serving
  * runtime (fp_server_*, fp_request_*); the plain-layout baseline
- * (fp_plain_*); statistics and probes (fp_count_leaves, fp_l2_read_probe);
+ * (fp_plain_*); statistics and probes (fp_count_leaves,
+ * fp_cardinality_from_leaf_counts, fp_infer_cardinality, fp_l2_read_probe);
  * status and fault injection (fp_sync_status, fp_inject_fault).
  *
  * Conventions for every entry point:
@@ -385,6 +386,40 @@ const char *fp_last_error(void);
  * Asynchronous on stream.  Errors: FP_EINVAL, FP_ECUDA. */
 int fp_count_leaves(const int32_t *out_leaf, int64_t n, int32_t n_trees, const int64_t *node_begin,
                     int64_t *leaf_count, int32_t *status, void *stream);
+
+/* Node cardinalities from leaf counts (Section III-A: the statistics behind
+ * the Stat ordering may be measured on observations after training).  For
+ * every tree of desc, a leaf's cardinality is its count and an internal
+ * node's is the sum of its two children's, so it is the number of counted
+ * observations whose path passes through the node; a node that no path from
+ * the root reaches gets 0.  Host only.
+ *   desc        host, caller-owned; its tree structure is read (and validated
+ *               as fp_pack_forest does)
+ *   leaf_count  host, int64 per node of desc (tree_node_begin[T] entries);
+ *               only the leaves' entries are read
+ *   out_card    host, int64 per node, overwritten; may be leaf_count itself
+ * Errors: FP_EINVAL (NULL argument, malformed forest), FP_ENOMEM. */
+int fp_cardinality_from_leaf_counts(const fp_forest_desc *desc, const int64_t *leaf_count, int64_t *out_card);
+
+/* Statistics inferred from observations, end to end (Section III-A): the
+ * resident forest classifies n observations in parity mode, the leaf each
+ * reaches in each tree is counted on the device (fp_count_leaves), and
+ * fp_cardinality_from_leaf_counts turns the counts into node cardinalities,
+ * which can be given to fp_pack_forest as desc->cardinality to order the
+ * layout by observed rather than training frequencies.
+ *   forest      resident forest packed from desc
+ *   desc        host, caller-owned: the same trees (counts of trees, features,
+ *               classes and internal nodes must match the forest's)
+ *   X           device, [n][n_features] FP32 row-major
+ *   chunk_rows  rows classified per parity launch (0: as many as 256 MiB of
+ *               leaf ids hold); device scratch for one chunk's leaf ids and
+ *               the counters comes from the stream-ordered pool
+ *   out_card    host, int64 per node of desc, overwritten
+ * Synchronises `stream`; a kernel error is reported (and the forest's status
+ * word cleared) as by fp_sync_status.  Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA,
+ * FP_EDEVICE, FP_ETIMEOUT. */
+int fp_infer_cardinality(const fp_device_forest *forest, const fp_forest_desc *desc, const float *X, int64_t n,
+                         int64_t chunk_rows, int64_t *out_card, void *stream);
 
 /* Measurement helper, no counterpart in the paper: time `iters` passes of
  * 16-byte reads over a device buffer of `bytes` (16-byte aligned; pick a size

@@ -75,7 +75,7 @@ EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload
            "fp_plain_predict_values", "fp_predict_host", "fp_predict_values_host", "fp_server_create",
            "fp_server_add_forest", "fp_server_start", "fp_server_submit", "fp_request_wait", "fp_request_latency",
            "fp_request_release", "fp_server_stop", "fp_server_stats", "fp_server_set_free_bytes",
-           "fp_server_release"]
+           "fp_server_release", "fp_cardinality_from_leaf_counts", "fp_infer_cardinality"]
 
 _lib = None
 _lock = threading.Lock()
@@ -134,6 +134,8 @@ def lib() -> ctypes.CDLL:
                 "fp_server_stats": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
                 "fp_server_set_free_bytes": ([P, i64], ctypes.c_int),
                 "fp_server_release": ([P], None),
+                "fp_cardinality_from_leaf_counts": ([ctypes.POINTER(fp_forest_desc), P, P], ctypes.c_int),
+                "fp_infer_cardinality": ([P, ctypes.POINTER(fp_forest_desc), P, i64, i64, P, P], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -535,44 +537,34 @@ def fp_count_leaves(out_leaf, node_begin, leaf_count, status, stream=None) -> No
     _check(lib().fp_count_leaves(lp, n, nt, nb, cp, sp, _stream_ptr(stream)), "fp_count_leaves")
 
 
-def infer_cardinality(forest, X, device_forest=None, stream=None):
+def fp_cardinality_from_leaf_counts(forest, leaf_count) -> np.ndarray:
+    """Node cardinalities from per-node leaf counts (host int64, one per node
+    of `forest`): the library sums each internal node from its children."""
+    keep = []
+    desc = make_desc(forest, keep)
+    cnt = _np(leaf_count, np.int64)
+    if cnt.shape != (forest.n_nodes,):
+        raise ValueError("leaf_count must hold one int64 per node")
+    out = np.empty(forest.n_nodes, np.int64)
+    _check(lib().fp_cardinality_from_leaf_counts(ctypes.byref(desc), cnt.ctypes.data, out.ctypes.data),
+           "fp_cardinality_from_leaf_counts")
+    return out
+
+
+def infer_cardinality(forest, X, device_forest=None, stream=None, chunk_rows: int = 0):
     """Cardinalities of every node of `forest` counted from the observations
-    X (CUDA float32 [n][n_features]): the leaves reached on the device
-    (fp_predict_leaves, fp_count_leaves), then each internal node the sum of
-    its children.  Returns an int64 numpy array aligned with the node arrays."""
+    X (CUDA float32 [n][n_features]) by fp_infer_cardinality: leaves reached
+    on the device, counted per node, each internal node the sum of its
+    children.  Returns an int64 numpy array aligned with the node arrays."""
     T = _torch()
     df = device_forest or fp_upload(fp_pack_forest(forest), stream)
-    leaves = df.predict_leaves(X, stream)
-    dev = X.device
-    nb = T.from_numpy(np.ascontiguousarray(forest.node_begin, dtype=np.int64)).to(dev)
-    counts = T.zeros(forest.n_nodes, dtype=T.int64, device=dev)
-    status = T.zeros(1, dtype=T.int32, device=dev)
-    fp_count_leaves(leaves, nb, counts, status, stream)
-    T.cuda.synchronize()
-    if int(status.item()) != FP_OK:
-        raise FPError(FP_EDEVICE, "fp_count_leaves: a leaf id was not a node of its tree")
-    card = counts.cpu().numpy()
-    left, right = np.asarray(forest.left), np.asarray(forest.right)
-    for t in range(forest.n_trees):
-        b, e = int(forest.node_begin[t]), int(forest.node_begin[t + 1])
-        # children before parents (post-order), whatever the node numbering
-        order = _postorder(left[b:e], right[b:e])
-        for v in order:
-            if left[b + v] >= 0:
-                card[b + v] = card[b + left[b + v]] + card[b + right[b + v]]
-    return card
-
-
-def _postorder(left, right):
-    out, stack = [], [(0, False)]
-    while stack:
-        v, done = stack.pop()
-        if done or left[v] < 0:
-            out.append(v)
-            continue
-        stack.append((v, True))
-        stack.append((int(right[v]), False))
-        stack.append((int(left[v]), False))
+    n = X.shape[0]
+    xp = _dptr(X, T.float32, (n, forest.n_features), "X")
+    keep = []
+    desc = make_desc(forest, keep)
+    out = np.empty(forest.n_nodes, np.int64)
+    _check(lib().fp_infer_cardinality(df.handle, ctypes.byref(desc), xp, n, chunk_rows, out.ctypes.data,
+                                      _stream_ptr(stream)), "fp_infer_cardinality")
     return out
 
 

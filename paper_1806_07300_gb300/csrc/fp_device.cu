@@ -839,3 +839,75 @@ extern "C" int fp_predict_values_host(const fp_device_forest *f, const float *X_
                              return fp_predict_values(f, Xd, rows, scale, bias, static_cast<float *>(outs[0]), s);
                          });
 }
+
+// ------------------------------------------- statistics from observations
+
+// Section III-A: the cardinalities that order a tree's nodes (Stat) may be
+// measured on observations instead of taken from training.  The rows go
+// through fp_predict_leaves in chunks (the leaf ids of one chunk sit in
+// scratch), fp_count_leaves adds them up per node on the device, and the
+// counts come back to the host, where each internal node becomes the sum of
+// its children (fp_cardinality_from_leaf_counts).
+extern "C" int fp_infer_cardinality(const fp_device_forest *f, const fp_forest_desc *desc, const float *X, int64_t n,
+                                    int64_t chunk_rows, int64_t *out_card, void *stream) {
+    if (!f || !desc || !out_card || n < 0 || chunk_rows < 0 || (n > 0 && !X) || !desc->tree_node_begin) {
+        fp_set_error("fp_infer_cardinality: bad arguments");
+        return FP_EINVAL;
+    }
+    const FpImageHeader &h = f->hdr;
+    if (desc->n_trees != h.n_trees || desc->n_features != h.n_features || desc->n_classes != h.n_classes) {
+        fp_set_error("fp_infer_cardinality: the descriptor (%d trees, %d features, %d classes) is not the forest's "
+                     "(%d, %d, %d)", desc->n_trees, desc->n_features, desc->n_classes, h.n_trees, h.n_features,
+                     h.n_classes);
+        return FP_EINVAL;
+    }
+    int64_t n_internal = 0;
+    const int64_t total = desc->tree_node_begin[desc->n_trees];
+    if (desc->left)
+        for (int64_t v = 0; v < total; ++v) n_internal += desc->left[v] >= 0;
+    if (!desc->left || n_internal != h.n_internal) {
+        fp_set_error("fp_infer_cardinality: the descriptor's internal nodes do not match the packed forest's");
+        return FP_EINVAL;
+    }
+    int rc = check_device(f);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t T = h.n_trees;
+    const int64_t chunk = std::max<int64_t>(
+        1, std::min<int64_t>(n, chunk_rows > 0 ? chunk_rows : std::max<int64_t>(1, (256 << 20) / (4 * T))));
+    auto align = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
+    const int64_t cnt_b = align(total * 8), nb_b = align((T + 1) * 8), st_b = 256;
+    const int64_t leaf_b = n > 0 ? align(chunk * T * 4) : 0;
+    void *block = nullptr;
+    rc = scratch_alloc(f->device, &block, (size_t)(cnt_b + nb_b + st_b + leaf_b), s);
+    if (rc) return rc;
+    uint8_t *base = static_cast<uint8_t *>(block);
+    int64_t *d_cnt = reinterpret_cast<int64_t *>(base);
+    int64_t *d_nb = reinterpret_cast<int64_t *>(base + cnt_b);
+    int32_t *d_st = reinterpret_cast<int32_t *>(base + cnt_b + nb_b);
+    int32_t *d_leaf = reinterpret_cast<int32_t *>(base + cnt_b + nb_b + st_b);
+    int32_t st = 0;
+    cudaError_t e = cudaMemsetAsync(block, 0, (size_t)(cnt_b + nb_b + st_b), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_nb, desc->tree_node_begin, (size_t)(T + 1) * 8, cudaMemcpyHostToDevice, s);
+    for (int64_t r0 = 0; e == cudaSuccess && rc == FP_OK && r0 < n; r0 += chunk) {
+        const int64_t rows = std::min<int64_t>(chunk, n - r0);
+        rc = fp_predict_leaves(f, X + r0 * h.n_features, rows, d_leaf, stream);
+        if (rc == FP_OK) rc = fp_count_leaves(d_leaf, rows, (int32_t)T, d_nb, d_cnt, d_st, stream);
+    }
+    if (e == cudaSuccess && rc == FP_OK)
+        e = cudaMemcpyAsync(out_card, d_cnt, (size_t)total * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && rc == FP_OK) e = cudaMemcpyAsync(&st, d_st, 4, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(block, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
+    if (rc != FP_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "fp_infer_cardinality");
+    if (st != 0) {
+        fp_set_error("fp_infer_cardinality: a leaf id was not a node of its tree");
+        return FP_EDEVICE;
+    }
+    rc = fp_sync_status(f, stream);  // an error the traversal kernel recorded
+    if (rc) return rc;
+    return fp_cardinality_from_leaf_counts(desc, out_card, out_card);
+}

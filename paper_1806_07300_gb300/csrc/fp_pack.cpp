@@ -826,3 +826,56 @@ extern "C" void fp_release_packed(fp_packed_forest *pf) { delete pf; }
 
 const FpImageHeader *fp_packed_header(const fp_packed_forest *pf) { return &pf->hdr; }
 const uint8_t *fp_packed_bytes(const fp_packed_forest *pf) { return pf->image.data(); }
+
+// Node cardinalities from leaf counts (Section III-A: the statistics that
+// order a tree's nodes may be measured on observations after training).  A
+// leaf keeps its count; an internal node gets the sum of its two children,
+// children before parents (an explicit post-order stack, so any node
+// numbering works); nodes no path reaches get 0.  out_card may alias
+// leaf_count.
+extern "C" int fp_cardinality_from_leaf_counts(const fp_forest_desc *desc, const int64_t *leaf_count,
+                                               int64_t *out_card) {
+    if (!desc || !leaf_count || !out_card || !desc->tree_node_begin || !desc->left || !desc->right ||
+        !desc->feature || !desc->leaf_class || desc->n_trees < 1 || desc->n_features < 1 || desc->n_classes < 1 ||
+        desc->tree_node_begin[0] != 0) {
+        fp_set_error("fp_cardinality_from_leaf_counts: bad arguments");
+        return FP_EINVAL;
+    }
+    try {
+        std::vector<uint8_t> seen;
+        std::vector<std::pair<int32_t, bool>> stack;
+        for (int32_t t = 0; t < desc->n_trees; ++t) {
+            const int64_t b = desc->tree_node_begin[t], e = desc->tree_node_begin[t + 1];
+            if (e < b) {
+                fp_set_error("fp_cardinality_from_leaf_counts: tree_node_begin not monotone at tree %d", t);
+                return FP_EINVAL;
+            }
+            TreeRef tr{desc->left + b, desc->right + b, desc->feature + b, desc->leaf_class + b, nullptr, nullptr,
+                       e - b};
+            int rc = validate_tree(tr, desc->n_features, desc->n_classes, t, seen);
+            if (rc) return rc;
+            const int64_t *cnt = leaf_count + b;
+            int64_t *card = out_card + b;
+            stack.assign(1, {0, false});
+            while (!stack.empty()) {
+                const auto [v, children_done] = stack.back();
+                stack.pop_back();
+                if (tr.leaf(v)) {
+                    card[v] = cnt[v];
+                } else if (children_done) {
+                    card[v] = card[tr.L[v]] + card[tr.R[v]];
+                } else {
+                    stack.push_back({v, true});
+                    stack.push_back({tr.R[v], false});
+                    stack.push_back({tr.L[v], false});
+                }
+            }
+            for (int64_t v = 0; v < tr.m; ++v)
+                if (!seen[(size_t)v]) card[v] = 0;
+        }
+        return FP_OK;
+    } catch (const std::bad_alloc &) {
+        fp_set_error("fp_cardinality_from_leaf_counts: out of host memory");
+        return FP_ENOMEM;
+    }
+}

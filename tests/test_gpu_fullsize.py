@@ -3,10 +3,9 @@
 The HBM-resident workload (256 trees, 4,000,000 rows) runs in every layout and
 launch the benchmark's autotuner may pick, and the image-shaped workload (128
 trees, 1,000,000 rows) in the library defaults and the tuner's candidates.
-Every row is checked against properties that hold at any size (votes sum to
-the tree count; the class is the first maximal vote); a seeded sample of rows
-is checked element by element against the oracle, votes, classes and per-tree
-leaf ids."""
+Every row's votes and class are compared element by element with the oracle's
+(computed once per workload on all host cores: about 80 s for the 4,000,000
+HBM rows), and a seeded sample of rows also by per-tree leaf id."""
 import numpy as np
 import pytest
 
@@ -62,23 +61,22 @@ def _check(df, forest, X, Xd, n):
     assert df.sync_status() == fp.FP_OK
     v = votes.cpu().numpy().astype(np.uint32)
     c = cls.cpu().numpy()
-    # properties of every row
-    assert np.all(v.sum(axis=1) == forest.n_trees)
-    np.testing.assert_array_equal(c, np.argmax(v, axis=1))
-    # seeded sample, element by element
     rng = np.random.Generator(np.random.PCG64(1234))
     idx = np.sort(rng.choice(n, size=min(SAMPLE, n), replace=False))
     idx[-1] = n - 1  # include the ragged last tile
     key = (id(forest), n)
     if key not in _REF:
         _REF.clear()
-        _REF[key] = oracle.predict(forest, X[idx], threads=oracle.default_threads())
-    ref = _REF[key]
-    np.testing.assert_array_equal(v[idx], ref["votes"])
-    np.testing.assert_array_equal(c[idx], ref["cls"])
+        full = oracle.predict(forest, X, leaves=False, threads=oracle.default_threads())
+        sample = oracle.predict(forest, X[idx], votes=False, classes=False, threads=oracle.default_threads())
+        _REF[key] = (full, sample["leaf"])
+    ref, ref_leaf = _REF[key]
+    # every row, element by element
+    np.testing.assert_array_equal(v, ref["votes"])
+    np.testing.assert_array_equal(c, ref["cls"])
     leaves = df.predict_leaves(torch.from_numpy(np.ascontiguousarray(X[idx])).cuda())
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
+    np.testing.assert_array_equal(leaves.cpu().numpy(), ref_leaf)
 
 
 @pytest.mark.parametrize("layout", HBM_LAYOUTS)

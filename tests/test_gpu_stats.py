@@ -80,3 +80,14 @@ def test_layout_ablation_preserves_predictions(name, n):
         np.testing.assert_array_equal(v.cpu().numpy().astype(np.uint32), ref["votes"])
         np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
         df.release()
+
+
+def test_inferred_cardinality_chunked_and_empty(tiny_forest, tiny_rows):
+    """The rows go through the device in chunks of any size with the same
+    counts; no rows give zero everywhere."""
+    X, _ = tiny_rows
+    Xd = torch.from_numpy(X).cuda()
+    whole = fp.infer_cardinality(tiny_forest, Xd)
+    for chunk in (1, 777, 4096):
+        np.testing.assert_array_equal(fp.infer_cardinality(tiny_forest, Xd, chunk_rows=chunk), whole)
+    assert not fp.infer_cardinality(tiny_forest, Xd[:0]).any()

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import datagen
+import oracle
 import paper_1806_07300_gb300 as fp
 
 torch = pytest.importorskip("torch")
@@ -39,8 +40,9 @@ def _call(df, X, votes, cls):
 
 @pytest.mark.parametrize("pass_bytes", [2048, -1])
 def test_noalloc_matches_fp_predict_twice(pass_bytes):
-    """Two calls in a row give exactly fp_predict's votes and classes, with
-    scratch in use (several passes) and without (one pass)."""
+    """Two calls in a row give exactly fp_predict's votes and classes, and
+    the oracle's, with scratch in use (several passes) and without (one
+    pass)."""
     X, y = datagen.rows("tiny", 0)
     forest = datagen.train_forest(X, y, 4, 16, 4, seed=0)
     pk = fp.fp_pack_forest(forest, bin_size=2, interleave_depth=2, pass_bytes=pass_bytes, obs_tile=128)
@@ -53,6 +55,9 @@ def test_noalloc_matches_fp_predict_twice(pass_bytes):
     ref_c = torch.empty((n,), dtype=torch.int32, device="cuda")
     fp.fp_predict(df, Xd, ref_v, ref_c)
     torch.cuda.synchronize()
+    want = oracle.predict(forest, Xt, leaves=False)
+    np.testing.assert_array_equal(ref_v.cpu().numpy().astype(np.uint32), want["votes"])
+    np.testing.assert_array_equal(ref_c.cpu().numpy(), want["cls"])
     for _ in range(2):
         v = torch.full((n, C), -1, dtype=torch.int32, device="cuda")
         c = torch.full((n,), -1, dtype=torch.int32, device="cuda")
