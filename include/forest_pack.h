@@ -299,7 +299,19 @@ int fp_predict_values_host(const fp_device_forest *forest, const float *X_host, 
  *   fp_server_stats         launches issued and admission waits so far
  *   fp_server_set_free_bytes  tests: the free device bytes admission sees
  *                           (-1: ask the device)
- *   fp_server_release       stops if needed and frees the server
+ *   fp_server_set_launch_timeout  the completion poll's limit per launch in
+ *                           seconds (default 60; >= 0)
+ *   fp_server_slots_in_service  slots not retired.  A slot returns to service
+ *                           only once all work queued on it has finished; a
+ *                           launch still running at its limit (or a failed
+ *                           launch whose queued copies are still running after
+ *                           another such wait) answers its requests with
+ *                           FP_ETIMEOUT and retires the slot, whose buffers
+ *                           are never reused; with no slot left in service
+ *                           every request is answered with FP_ETIMEOUT
+ *   fp_server_release       stops if needed and frees the server (a retired
+ *                           slot's buffers are freed only if its work has
+ *                           finished within one more launch limit)
  * Errors: FP_EINVAL, FP_ENOMEM, FP_ECUDA; a failed launch answers its
  * requests with its status. */
 typedef struct fp_server fp_server;
@@ -316,6 +328,8 @@ void fp_request_release(fp_request *request);
 int fp_server_stop(fp_server *server);
 int fp_server_stats(const fp_server *server, int64_t *launches, int64_t *rejected_for_memory);
 int fp_server_set_free_bytes(fp_server *server, int64_t free_bytes);
+int fp_server_set_launch_timeout(fp_server *server, double seconds);
+int fp_server_slots_in_service(const fp_server *server, int32_t *out);
 void fp_server_release(fp_server *server);
 
 /* Parity mode: the leaf each observation reaches in each tree.

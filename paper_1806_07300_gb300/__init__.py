@@ -75,7 +75,8 @@ EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload
            "fp_plain_predict_values", "fp_predict_host", "fp_predict_values_host", "fp_server_create",
            "fp_server_add_forest", "fp_server_start", "fp_server_submit", "fp_request_wait", "fp_request_latency",
            "fp_request_release", "fp_server_stop", "fp_server_stats", "fp_server_set_free_bytes",
-           "fp_server_release", "fp_cardinality_from_leaf_counts", "fp_infer_cardinality"]
+           "fp_server_release", "fp_cardinality_from_leaf_counts", "fp_infer_cardinality",
+           "fp_server_set_launch_timeout", "fp_server_slots_in_service"]
 
 _lib = None
 _lock = threading.Lock()
@@ -134,6 +135,8 @@ def lib() -> ctypes.CDLL:
                 "fp_server_stats": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
                 "fp_server_set_free_bytes": ([P, i64], ctypes.c_int),
                 "fp_server_release": ([P], None),
+                "fp_server_set_launch_timeout": ([P, ctypes.c_double], ctypes.c_int),
+                "fp_server_slots_in_service": ([P, ctypes.POINTER(i32)], ctypes.c_int),
                 "fp_cardinality_from_leaf_counts": ([ctypes.POINTER(fp_forest_desc), P, P], ctypes.c_int),
                 "fp_infer_cardinality": ([P, ctypes.POINTER(fp_forest_desc), P, i64, i64, P, P], ctypes.c_int),
             }

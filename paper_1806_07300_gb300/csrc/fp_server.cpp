@@ -12,7 +12,11 @@
 // (plus a margin), else it waits for launches in flight to finish.  A
 // completion thread polls each launch's event in order (bounded: 60 s),
 // copies every request's classes (and votes) into the caller's buffers and
-// wakes its waiters.  Latency runs from submit to completion.
+// wakes its waiters.  Latency runs from submit to completion.  A slot goes
+// back into service only once everything queued on it has finished; a slot
+// whose work did not finish within the limit is retired (its buffers may
+// still be in use), and with no slot left in service requests are answered
+// with FP_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,6 +63,7 @@ struct Slot {
     size_t dev_cap = 0;
     std::vector<Entry> entries;
     int status = FP_OK;
+    bool retired = false;  // work on it outlived the completion poll; never reused
 };
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -82,6 +87,8 @@ struct fp_server {
     bool started = false, stopping = false, batcher_done = false, joined = false;
     int64_t launches = 0, rejected_for_memory = 0;
     int64_t free_override = -1;  // reported free device bytes for tests (-1: ask the device)
+    double launch_timeout_s = 60.0;  // completion poll per launch
+    int32_t live_slots = 0;          // slots not retired
 };
 
 namespace {
@@ -236,12 +243,25 @@ void batch_loop(fp_server *s) {
             ++s->rejected_for_memory;
             s->cv_slot.wait_for(lk, std::chrono::milliseconds(1));
         }
-        int si;
+        int si = -1;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_slot.wait(lk, [&] { return !s->free_slots.empty(); });
-            si = s->free_slots.back();
-            s->free_slots.pop_back();
+            s->cv_slot.wait(lk, [&] { return !s->free_slots.empty() || s->live_slots == 0; });
+            if (!s->free_slots.empty()) {
+                si = s->free_slots.back();
+                s->free_slots.pop_back();
+            } else {  // every slot retired: nothing can run this batch
+                const auto t = fp_clock::now();
+                for (fp_request *r : batch) {
+                    r->status = FP_ETIMEOUT;
+                    r->t_done = t;
+                    r->done = true;
+                }
+            }
+        }
+        if (si < 0) {
+            s->cv_done.notify_all();
+            continue;
         }
         Slot &sl = s->slot[si];
         sl.status = launch(s, sl, groups, gforest);
@@ -275,18 +295,26 @@ void complete_loop(fp_server *s) {
         }
         Slot &sl = s->slot[si];
         int st = sl.status;
-        const auto deadline = fp_clock::now() + std::chrono::seconds(60);
-        while (st == FP_OK) {  // bounded poll of the launch's completion
-            const cudaError_t q = cudaEventQuery(sl.ev);
-            if (q == cudaSuccess) break;
-            if (q != cudaErrorNotReady) {
-                st = FP_ECUDA;
-            } else if (fp_clock::now() > deadline) {
-                st = FP_ETIMEOUT;
-            } else {
+        const auto limit = std::chrono::duration_cast<fp_clock::duration>(
+            std::chrono::duration<double>(s->launch_timeout_s));
+        // bounded poll of the slot's event: 1 = done, 0 = not done by the deadline, -1 = CUDA error
+        auto poll = [&](fp_clock::time_point deadline) {
+            for (;;) {
+                const cudaError_t q = cudaEventQuery(sl.ev);
+                if (q == cudaSuccess) return 1;
+                if (q != cudaErrorNotReady) return -1;
+                if (fp_clock::now() > deadline) return 0;
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
+        };
+        int idle = 0;
+        if (st == FP_OK) {
+            idle = poll(fp_clock::now() + limit);
+            if (idle != 1) st = idle < 0 ? FP_ECUDA : FP_ETIMEOUT;
+        } else {  // a failed launch may have queued work before it failed: let it drain, bounded
+            idle = poll(fp_clock::now() + limit);
         }
+        if (st == FP_ETIMEOUT && idle == 0) idle = poll(fp_clock::now());  // one last look
         const auto t = fp_clock::now();
         if (st == FP_OK) {
             for (const Entry &en : sl.entries) {
@@ -305,7 +333,12 @@ void complete_loop(fp_server *s) {
             }
             sl.entries.clear();
             s->inflight.pop_front();
-            s->free_slots.push_back(si);
+            if (idle == 1) {
+                s->free_slots.push_back(si);
+            } else {  // its copies or kernel may still touch its buffers
+                sl.retired = true;
+                --s->live_slots;
+            }
         }
         s->cv_done.notify_all();
         s->cv_slot.notify_all();
@@ -351,6 +384,7 @@ extern "C" int fp_server_create(int32_t device, int32_t slots, int64_t max_rows,
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slot[i].ev, cudaEventDisableTiming);
         s->free_slots.push_back(slots - 1 - i);
     }
+    s->live_slots = slots;
     if (e != cudaSuccess) {
         fp_set_error("fp_server_create: %s", cudaGetErrorString(e));
         fp_server_release(s);
@@ -495,14 +529,46 @@ extern "C" int fp_server_set_free_bytes(fp_server *s, int64_t free_bytes) {
     return FP_OK;
 }
 
+extern "C" int fp_server_set_launch_timeout(fp_server *s, double seconds) {
+    if (!s || !(seconds >= 0)) {
+        fp_set_error("fp_server_set_launch_timeout: bad arguments");
+        return FP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->launch_timeout_s = seconds;
+    return FP_OK;
+}
+
+extern "C" int fp_server_slots_in_service(const fp_server *s, int32_t *out) {
+    if (!s || !out) {
+        fp_set_error("fp_server_slots_in_service: bad arguments");
+        return FP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(const_cast<fp_server *>(s)->mu);
+    *out = s->live_slots;
+    return FP_OK;
+}
+
 extern "C" void fp_server_release(fp_server *s) {
     if (!s) return;
     join_threads(s);
     cudaSetDevice(s->device);
     for (Slot &sl : s->slot) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.dev) cudaFree(sl.dev);
-        if (sl.pin) cudaFreeHost(sl.pin);
+        bool idle = true;
+        if (sl.retired && sl.ev) {  // its work outlived the completion poll: wait once more, bounded
+            const auto deadline = fp_clock::now() + std::chrono::duration_cast<fp_clock::duration>(
+                                                        std::chrono::duration<double>(s->launch_timeout_s));
+            cudaError_t q;
+            while ((q = cudaEventQuery(sl.ev)) == cudaErrorNotReady && fp_clock::now() <= deadline)
+                std::this_thread::sleep_for(std::chrono::microseconds(100));
+            idle = q == cudaSuccess;
+        } else if (sl.stream) {
+            cudaStreamSynchronize(sl.stream);  // idle already: every launch on it completed
+        }
+        if (idle) {  // else the buffers stay allocated: work that never finished may still use them
+            if (sl.dev) cudaFree(sl.dev);
+            if (sl.pin) cudaFreeHost(sl.pin);
+        }
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }

@@ -181,6 +181,18 @@ class ForestServer:
     def rejected_for_memory(self) -> int:
         return self._stats()[1]
 
+    @property
+    def slots_in_service(self) -> int:
+        """Slots not retired (a slot whose launch outlived the completion
+        poll's limit is never reused)."""
+        v = ctypes.c_int32()
+        _check(lib().fp_server_slots_in_service(self._h, ctypes.byref(v)), "fp_server_slots_in_service")
+        return v.value
+
+    def set_launch_timeout(self, seconds: float) -> None:
+        """The completion poll's limit per launch (default 60 s)."""
+        _check(lib().fp_server_set_launch_timeout(self._h, float(seconds)), "fp_server_set_launch_timeout")
+
     def set_free_bytes(self, free_bytes: int) -> None:
         """Tests: the free device memory the admission check sees (-1: the device's)."""
         _check(lib().fp_server_set_free_bytes(self._h, int(free_bytes)), "fp_server_set_free_bytes")

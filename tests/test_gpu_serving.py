@@ -141,3 +141,52 @@ def test_failed_launch_answers_its_requests(served):
         assert good.wait(60) and good.error is None
         np.testing.assert_array_equal(good.classes, oracle.predict(forests["tiny"], rows["tiny"][40:90],
                                                                    leaves=False)["cls"])
+
+
+def test_launch_past_its_limit_retires_its_slot(served):
+    """A launch still running when the completion poll's limit runs out is
+    answered with FP_ETIMEOUT and its slot is retired, never reused while its
+    work may still touch the slot's buffers; the other slot keeps serving
+    exact answers; with no slot left in service a request is answered with
+    FP_ETIMEOUT at once instead of waiting.  The slow launch is made on the
+    host side: the forest's bin waits ignore completed copies until their
+    bounded poll gives up (the kernel then ends by itself)."""
+    import paper_1806_07300_gb300 as fp
+    forests, rows = served
+    X = rows["tiny"]
+
+    def stall(srv, on):
+        df = srv.forests["tiny"].df
+        fp.fp_inject_fault(df, fp.FP_FAULT_WAIT_LIMIT, (1 << 18) if on else (1 << 24))
+        fp.fp_inject_fault(df, fp.FP_FAULT_STALL_BIN_COPY, 1 if on else 0)
+        srv.set_launch_timeout(0.0 if on else 60.0)
+
+    srv = _server(forests, slots=2)
+    with srv:
+        warm = srv.submit("tiny", X[:64])
+        assert warm.wait(60) and warm.error is None
+        stall(srv, True)
+        slow = srv.submit("tiny", X[:500])
+        assert slow.wait(60) and slow.error == "FP_ETIMEOUT"
+        assert srv.slots_in_service == 1
+        stall(srv, False)
+        good = [srv.submit("tiny", X[i * 100: (i + 1) * 100]) for i in range(20)]
+        for i, h in enumerate(good):
+            assert h.wait(60) and h.error is None
+            np.testing.assert_array_equal(h.classes, oracle.predict(forests["tiny"], X[i * 100: (i + 1) * 100],
+                                                                    leaves=False)["cls"])
+        assert srv.slots_in_service == 1
+    srv.forests["tiny"].df.sync_status()  # the slow kernel recorded its timeout; clear it
+    srv.close()
+
+    one = _server(forests, slots=1)
+    with one:
+        stall(one, True)
+        slow = one.submit("tiny", X[:500])
+        assert slow.wait(60) and slow.error == "FP_ETIMEOUT"
+        assert one.slots_in_service == 0
+        stall(one, False)
+        after = one.submit("tiny", X[:10])
+        assert after.wait(60) and after.error == "FP_ETIMEOUT"
+    one.forests["tiny"].df.sync_status()
+    one.close()
