@@ -70,7 +70,7 @@ WORKLOADS = {
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
 # (B, d, head_select[, deep_levels]); without deep_levels the library's default (three levels here)
-HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (2, 9, 2), (1, 11, 2), (4, 9, 1), (3, 8, 3), (3, 9, 2, 2)]
+HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (5, 9, 2), (1, 11, 2), (4, 9, 1), (3, 8, 3), (3, 9, 2, 2)]
 HBM_LAUNCHES = [(1024, 32, 16, 2), (1024, 32, 24, 2), (768, 32, 16, 2), (1024, 32, 16, 3)]  # tile, warps, refill, buffers
 # the value workloads: the regression forest's trees resemble the hbm ones; the
 # boosted trees (depth <= 6) fit whole in a level head of depth 5
@@ -108,7 +108,7 @@ def parse():
     ap.add_argument("--bin-buffers", type=int, default=0)
     ap.add_argument("--deep-levels", type=int, default=0, help="tree levels per super-node: 2, 3 (0: default)")
     ap.add_argument("--pass-bytes", type=int, default=0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of requests per offered rate")
     return ap.parse_args()
 
 
@@ -171,10 +171,11 @@ def measured_peaks():
 
 def kernel_fingerprint() -> str:
     """Hash of the sources that decide the traversal kernel's memory traffic:
-    the kernel, the image format and the packer (the launch parameters are
-    matched per captured entry)."""
+    the kernel, the image format, the packer and the launch set-up (grid,
+    tile shrinking, scratch); the launch parameters are matched per captured
+    entry."""
     h = hashlib.sha1()
-    for name in ("fp_traverse.cuh", "fp_pack.cpp", "fp_internal.h"):
+    for name in ("fp_traverse.cuh", "fp_pack.cpp", "fp_internal.h", "fp_device.cu"):
         with open(os.path.join(ROOT, "paper_1806_07300_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -198,10 +199,26 @@ def profiled_entry(workload: str, params: dict):
 
 
 def profiled_traffic(workload: str, params: dict, rows: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to `rows`
-    (traffic grows with the rows swept), or None (see profiled_entry)."""
+    """DRAM bytes per launch from the committed ncu summary and how they were
+    obtained: measured at these rows, or scaled linearly from the captured
+    row count (an extrapolation: the rows are re-read once per pass, but the
+    forest's L2 reuse need not scale with the rows).  (None, reason) when the
+    kernel changed since the capture or the parameters were not captured."""
     e = profiled_entry(workload, params)
-    return None if e is None else e["dram_bytes_per_launch"] * rows / e["rows"]
+    if e is None:
+        return None, "no ncu capture for this kernel source and launch configuration"
+    if e["rows"] == rows:
+        return e["dram_bytes_per_launch"], f"ncu, one launch over {rows} rows"
+    return e["dram_bytes_per_launch"] * rows / e["rows"], \
+        f"ncu at {e['rows']} rows, scaled linearly to {rows} rows (extrapolated)"
+
+
+def check_roofline(r: dict) -> None:
+    """A fraction far above 1 means the bound is misapplied (bytes that never
+    touch the resource): refuse to print it."""
+    for k, v in [("frac", r.get("frac")), ("hbm.frac", (r.get("hbm") or {}).get("frac"))]:
+        if v is not None and v > 1.2:
+            raise RuntimeError(f"roofline {k} = {v:.2f} > 1.2: the bound does not describe this kernel")
 
 
 def cpu_sample(forest, X, target_s: float, threads: int):
@@ -470,7 +487,7 @@ def run_packed(args, ws, rank, local):
     peak, peak_kind = measured_peaks()
     params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "obs_tile",
                                    "warps_per_cta", "refill_lanes", "bin_buffers")}
-    traffic = profiled_traffic(name, params, n)
+    traffic, traffic_how = profiled_traffic(name, params, n)
     # the sector-granular figure: 32 B per global-load sector the kernel touched
     # (ncu, same launch configuration), the practical bound beside the
     # algorithmic 8 B per node visit
@@ -482,6 +499,15 @@ def run_packed(args, ws, rank, local):
                    "source": "ncu l1tex__t_sectors / l1tex__t_requests_pipe_lsu_mem_global_op_ld, one launch"}
     kernel = "fp_traverse_kernel<values>" if values else "fp_traverse_kernel<votes>"
     visits_per_s = visits_per_obs * n / (avg_launch_ms / 1e3)
+    launch_s = avg_launch_ms / 1e3
+    hbm_sub = {"peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+               "dram_gbs": None if traffic is None else traffic / launch_s / 1e9,
+               "frac": None if traffic is None else traffic / launch_s / 1e9 / peak,
+               "traffic": traffic, "traffic_source": traffic_how,
+               "algorithmic_frac": achieved / peak,
+               "note": "the forest's nodes come from shared memory (interleaved heads) and L2, so DRAM moves a "
+                       "small part of the algorithmic bytes; algorithmic_frac divides algorithmic bytes by the "
+                       "HBM copy bandwidth and is not a DRAM fraction"}
     if info["n_super"] == 0:
         # every internal node sits in the bins' interleaved heads: the node
         # reads come from shared memory, so the bound is the SMs' shared-memory
@@ -493,19 +519,22 @@ def run_packed(args, ws, rank, local):
                     "frac": smem_achieved / smem_peak, "traffic": traffic,
                     "peak_kind": f"derived: shared-memory loads, {sms} SMs x 128 B/clock x max SM clock",
                     "kernel": kernel, "avg_launch_ms": avg_launch_ms, "bytes_per_obs": 8.0 * visits_per_obs,
-                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s,
-                    "hbm": {"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                            "note": "algorithmic bytes incl. node records served from shared memory"}}
+                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s, "hbm": hbm_sub}
     else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
-                    "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
-                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s,
-                    "l2": {"peak": l2_gbs, "achieved": achieved, "frac": achieved / l2_gbs, "unit": "GB/s",
-                           "peak_kind": "measured by fp_l2_read_probe (64 MiB, 16-byte loads)"},
+        # the node fetches below the heads draw on L2 (the forest's passes stay
+        # L2-resident): the headline fraction is of the measured L2 read
+        # bandwidth; DRAM is reported beside it from the ncu counters
+        roofline = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
+                    "frac": achieved / l2_gbs, "traffic": traffic,
+                    "peak_kind": "measured in this run: fp_l2_read_probe, 16-byte loads over a 64 MiB "
+                                 "L2-resident buffer",
+                    "kernel": kernel, "avg_launch_ms": avg_launch_ms, "bytes_per_obs": bytes_per_obs,
+                    "bytes_per_obs_kind": "algorithmic: 8 B per internal node visited (oracle count) + row + outputs",
+                    "visits_per_obs": visits_per_obs, "node_visits_per_s": visits_per_s, "hbm": hbm_sub,
                     "sector_granular": None if sectors is None else dict(
-                        sectors, achieved_gbs=sectors["bytes_per_obs"] * n / (avg_launch_ms / 1e3) / 1e9,
-                        frac_of_l2=sectors["bytes_per_obs"] * n / (avg_launch_ms / 1e3) / 1e9 / l2_gbs)}
+                        sectors, achieved_gbs=sectors["bytes_per_obs"] * n / launch_s / 1e9,
+                        frac_of_l2=sectors["bytes_per_obs"] * n / launch_s / 1e9 / l2_gbs)}
+    check_roofline(roofline)
     out = base_line(args, ws, value, total_ms,
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
                      "n_classes": C, **params, "passes": info["passes"], "forest_bytes": info["total_bytes"],
@@ -535,9 +564,14 @@ def run_packed(args, ws, rank, local):
 
 def run_batched(args, ws, rank, local):
     """The batched workload: one persistent launch over 8 forests and uneven
-    batches, captured once in a CUDA graph and replayed every step."""
+    batches, captured once in a CUDA graph and replayed every step.  After the
+    timed replays every row's votes and class are compared with the oracle,
+    whose run on the same batches is also the CPU baseline; the end-to-end leg
+    copies each step's rows in from pinned host memory, replays the graph and
+    copies the classes back."""
     import torch
     import datagen
+    import oracle
     import paper_1806_07300_gb300 as fp
     from paper_1806_07300_gb300 import autotune as at
 
@@ -574,15 +608,81 @@ def run_batched(args, ws, rank, local):
     total_ms = a.elapsed_time(b)
     rows = sum(sizes)
     value = ws * rows * args.steps / (total_ms / 1e3)
+    for d in dfs:
+        if d.sync_status() != fp.FP_OK:
+            raise RuntimeError(f"kernel status: {fp.fp_last_error()}")
+    got_v = [v.cpu().numpy().astype(np.uint32) for v in votes]
+    got_c = [c.cpu().numpy() for c in cls]
+
+    # end to end: rows from pinned host memory into the graph's inputs, one
+    # replay, classes back to pinned host memory, every step
+    Xpin = [torch.from_numpy(x).pin_memory() for x in Xh]
+    cls_host = [torch.empty((x.shape[0],), dtype=torch.int32).pin_memory() for x in Xh]
+
+    def e2e_step():
+        for x, xp in zip(Xs, Xpin):
+            x.copy_(xp, non_blocking=True)
+        g.replay()
+        for c, ch in zip(cls, cls_host):
+            ch.copy_(c, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record()
+    for _ in range(e2e_steps):
+        e2e_step()
+    b2.record()
+    torch.cuda.synchronize()
+    e2e_ms = a2.elapsed_time(b2) / e2e_steps
+    for c, ch in zip(got_c, cls_host):
+        if not np.array_equal(c, ch.numpy()):
+            raise RuntimeError("end-to-end classes differ from the device path's")
+    e2e = {"value": ws * rows / (e2e_ms / 1e3), "unit": "observations/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(sum(x.nbytes for x in Xh)), "d2h_bytes_per_step": int(4 * rows),
+           "path": "pinned rows copied into the captured inputs, graph replay (fp_predict_batched), classes "
+                   "copied back"}
+    l2_gbs = fp.fp_l2_read_probe(64 << 20, 40, stream=stream)
     if rank != 0:
         return
+
+    # the oracle on every row of every batch: parity and the CPU baseline
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    refs = [oracle.predict(f, x, leaves=False, threads=threads) for f, x in zip(forests, Xh)]
+    cpu_s = time.perf_counter() - t0
+    mism = sum(int((gv != r["votes"]).any(axis=1).sum()) + int((gc != r["cls"]).sum())
+               for gv, gc, r in zip(got_v, got_c, refs))
+    if mism:
+        raise RuntimeError(f"batched workload: {mism} rows differ from the oracle")
+    visits = sum(r["visits"] for r in refs)
+    algo_bytes = 8.0 * visits + sum(x.shape[0] * (4.0 * x.shape[1] + 4.0 * f.n_classes + 4.0)
+                                    for f, x in zip(forests, Xh))
+    launch_s = total_ms / args.steps / 1e3
+    achieved = algo_bytes / launch_s / 1e9
+    peak_hbm, peak_kind = measured_peaks()
+    roofline = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+                "traffic": None, "traffic_source": "not captured for this launch",
+                "peak_kind": "measured in this run: fp_l2_read_probe, 16-byte loads over a 64 MiB L2-resident buffer",
+                "kernel": "fp_traverse_batched_kernel", "avg_launch_ms": total_ms / args.steps,
+                "bytes_per_launch": algo_bytes,
+                "bytes_kind": "algorithmic: 8 B per internal node visited (oracle count) + rows + votes + classes",
+                "node_visits_per_s": visits / launch_s,
+                "hbm": {"peak": peak_hbm, "peak_kind": peak_kind, "algorithmic_frac": achieved / peak_hbm,
+                        "note": "forests and rows stay L2-resident across replays; not a DRAM fraction"}}
+    check_roofline(roofline)
     out = base_line(args, ws, value, total_ms,
                     {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
                      "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
-                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "launch")},
+                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels",
+                                                       "launch")},
                      "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
     out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
-                "e2e": None, "roofline": None, "cpu_baseline": None})
+                "e2e": e2e, "roofline": roofline,
+                "parity_checked": {"rows": rows, "mismatches": 0, "compared": "votes and class of every row"},
+                "cpu_baseline": {"value": rows / cpu_s, "unit": "observations/s", "cores": threads, "kind": "oracle",
+                                 "sample": f"all {rows} rows of the 8 batches ({cpu_s:.1f} s)"}})
     print(json.dumps(out))
 
 
@@ -604,6 +704,7 @@ def run_serving(args, ws, rank, local):
     rng = np.random.Generator(np.random.PCG64(11))
     keys = sorted(forests)
     results = []
+    all_reqs = []
     with srv:
         # warm every forest once
         for k in keys:
@@ -630,6 +731,7 @@ def run_serving(args, ws, rank, local):
             t0 = time.perf_counter()
             for r in reqs:
                 r.wait(120)
+            all_reqs.extend(reqs)
             wall = args.serve_seconds + (time.perf_counter() - t0)
             lat = latency_summary(reqs)
             results.append({"rate_rps": rate, "requests": len(reqs), "rows": n_rows, "obs_per_s": n_rows / wall,
@@ -638,13 +740,68 @@ def run_serving(args, ws, rank, local):
     if rank != 0:
         return
     best = max(results, key=lambda r: r["obs_per_s"])
+    # every answer against the oracle (after the timed window), per forest; the
+    # oracle's time over the same rows is the CPU baseline, and its visit counts
+    # give the algorithmic bytes behind the best rate
+    import oracle
+    threads = oracle.default_threads()
+    checked = mism = 0
+    cpu_s = 0.0
+    visits_per_row = {}
+    for k in keys:
+        mine = [r for r in all_reqs if r.forest == k]
+        visits = rows_k = 0
+        i = 0
+        while i < len(mine):  # chunks of about 100k rows keep the host copies small
+            j, m = i, 0
+            while j < len(mine) and (j == i or m + mine[j].X.shape[0] <= 100_000):
+                m += mine[j].X.shape[0]
+                j += 1
+            X = np.concatenate([r.X for r in mine[i:j]])
+            t0 = time.perf_counter()
+            ref = oracle.predict(forests[k], X, leaves=False, votes=False, threads=threads)
+            cpu_s += time.perf_counter() - t0
+            mism += int((np.concatenate([r.classes for r in mine[i:j]]) != ref["cls"]).sum())
+            visits += ref["visits"]
+            rows_k += m
+            i = j
+        checked += rows_k
+        if rows_k:
+            visits_per_row[k] = visits / rows_k
+    if mism:
+        raise RuntimeError(f"serving: {mism} of {checked} answers differ from the oracle")
+    bytes_per_row = {k: 8.0 * visits_per_row[k] + 4.0 * forests[k].n_features + 4.0 for k in visits_per_row}
+    mean_bytes = sum(bytes_per_row.values()) / len(bytes_per_row)  # forests are chosen uniformly
+    l2_gbs = fp_l2_probe(local)
+    achieved = best["obs_per_s"] * mean_bytes / 1e9
+    roofline = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+                "traffic": None, "traffic_source": "not captured for a request stream",
+                "peak_kind": "measured in this run: fp_l2_read_probe, 16-byte loads over a 64 MiB L2-resident buffer",
+                "kernel": "fp_traverse_batched_kernel (launched by the serving runtime)",
+                "bytes_per_obs": mean_bytes,
+                "bytes_kind": "algorithmic per row, averaged over the four forests (chosen uniformly): 8 B per "
+                              "internal node visited (oracle count) + row + class",
+                "note": f"over the wall time of the {best['rate_rps']} req/s window: the offered request rate, not "
+                        "the GPU, sets the throughput"}
+    check_roofline(roofline)
     out = base_line(args, ws, best["obs_per_s"] * ws, 1e3 * args.serve_seconds,
                     {"workload": "serving", "desc": WORKLOADS["serving"]["desc"], "slots": srv.slots,
                      "parallelism": f"replicas x{ws}", "l2": "not applicable (request stream)"})
+    out["steps"], out["ms_per_step"] = len(results), 1e3 * args.serve_seconds  # one step = one offered rate's window
     out.update({"serving": results, "launches": srv.launches, "gpu_launches": srv.launches,
-                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "e2e": None, "roofline": None,
-                "cpu_baseline": None})
+                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "e2e": None, "roofline": roofline,
+                "parity_checked": {"rows": checked, "requests": len(all_reqs), "mismatches": 0,
+                                   "compared": "class of every row of every request"},
+                "cpu_baseline": {"value": checked / cpu_s, "unit": "observations/s", "cores": threads,
+                                 "kind": "oracle", "sample": f"the {checked} served rows ({cpu_s:.1f} s)"}})
     print(json.dumps(out))
+
+
+def fp_l2_probe(local: int) -> float:
+    import torch
+    import paper_1806_07300_gb300 as fp
+    with torch.cuda.device(local):
+        return fp.fp_l2_read_probe(64 << 20, 40)
 
 
 # ----------------------------------------------------------------- ablation

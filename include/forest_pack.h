@@ -24,7 +24,8 @@
  * fp_predict_values, fp_predict_leaves, fp_predict_batched,
  * fp_predict_noalloc); classification of host rows with copies pipelined
  * against the kernels (fp_predict_host, fp_predict_values_host); the serving
- * runtime (fp_server_*, fp_request_*); the plain-layout baseline
+ * runtime (fp_server_*, fp_request_*); tree-bin sharding over processes
+ * (fp_shard_trees, fp_pack_forest_trees, fp_votes_argmax); the plain-layout baseline
  * (fp_plain_*); statistics and probes (fp_count_leaves,
  * fp_cardinality_from_leaf_counts, fp_infer_cardinality, fp_l2_read_probe);
  * status and fault injection (fp_sync_status, fp_inject_fault).
@@ -434,6 +435,42 @@ int fp_cardinality_from_leaf_counts(const fp_forest_desc *desc, const int64_t *l
  * FP_EDEVICE, FP_ETIMEOUT. */
 int fp_infer_cardinality(const fp_device_forest *forest, const fp_forest_desc *desc, const float *X, int64_t n,
                          int64_t chunk_rows, int64_t *out_card, void *stream);
+
+/* ---- Tree-bin sharding over processes (Section III: the T/B bins of a
+ * forest are bound to processes; Section IV-E scales that over machines).
+ * Every process packs the same forest's bins for its shard, classifies the
+ * same rows with them (fp_predict with out_votes), the per-class votes are
+ * summed over processes by the caller's collective (for example an NCCL
+ * all-reduce of the [n][n_classes] uint32 array), and fp_votes_argmax turns
+ * the sums into classes.  Because every tree belongs to exactly one shard,
+ * the summed votes and the classes equal the whole forest's.
+ *
+ * fp_shard_trees: the trees of shard `shard` of n_shards, whole bins of
+ * bin_size consecutive trees, in contiguous runs cut so that each shard's
+ * expected work is as even as the bin boundaries allow.  A tree's work is its
+ * expected number of internal nodes visited per observation, the sum of its
+ * internal nodes' cardinalities divided by its root's (Section III-A's
+ * training statistics), or its internal node count when desc has no
+ * cardinalities.  Host only; every process computes the same split.
+ *   *tree_begin, *tree_end   trees [begin, end) of desc; an empty range when
+ *                            there are fewer bins than shards
+ * Errors: FP_EINVAL, FP_ENOMEM. */
+int fp_shard_trees(const fp_forest_desc *desc, int32_t bin_size, int32_t n_shards, int32_t shard,
+                   int32_t *tree_begin, int32_t *tree_end);
+
+/* fp_pack_forest over the trees [tree_begin, tree_end) of desc alone (a
+ * shard), as a forest of tree_end - tree_begin trees; leaf ids stay the
+ * trees' own node ids.  Errors: as fp_pack_forest, FP_EINVAL for an empty or
+ * out-of-range tree range. */
+int fp_pack_forest_trees(const fp_forest_desc *desc, const fp_pack_params *params, int32_t tree_begin,
+                         int32_t tree_end, fp_packed_forest **out);
+
+/* The class of each row from its (summed) votes: out_class[i] = the first c
+ * with the largest votes[i][c] (lowest class on ties, as fp_predict).
+ *   votes      device, [n][n_classes] uint32
+ *   out_class  device, [n] int32
+ * Asynchronous on `stream`.  Errors: FP_EINVAL, FP_ECUDA. */
+int fp_votes_argmax(const uint32_t *votes, int64_t n, int32_t n_classes, int32_t *out_class, void *stream);
 
 /* Measurement helper, no counterpart in the paper: time `iters` passes of
  * 16-byte reads over a device buffer of `bytes` (16-byte aligned; pick a size

@@ -76,7 +76,8 @@ EXPORTS = ["fp_pack_forest", "fp_packed_info_get", "fp_packed_image", "fp_upload
            "fp_server_add_forest", "fp_server_start", "fp_server_submit", "fp_request_wait", "fp_request_latency",
            "fp_request_release", "fp_server_stop", "fp_server_stats", "fp_server_set_free_bytes",
            "fp_server_release", "fp_cardinality_from_leaf_counts", "fp_infer_cardinality",
-           "fp_server_set_launch_timeout", "fp_server_slots_in_service"]
+           "fp_server_set_launch_timeout", "fp_server_slots_in_service", "fp_shard_trees", "fp_pack_forest_trees",
+           "fp_votes_argmax"]
 
 _lib = None
 _lock = threading.Lock()
@@ -136,6 +137,11 @@ def lib() -> ctypes.CDLL:
                 "fp_server_set_free_bytes": ([P, i64], ctypes.c_int),
                 "fp_server_release": ([P], None),
                 "fp_server_set_launch_timeout": ([P, ctypes.c_double], ctypes.c_int),
+                "fp_shard_trees": ([ctypes.POINTER(fp_forest_desc), i32, i32, i32, ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32)], ctypes.c_int),
+                "fp_pack_forest_trees": ([ctypes.POINTER(fp_forest_desc), ctypes.POINTER(fp_pack_params), i32, i32,
+                                          ctypes.POINTER(P)], ctypes.c_int),
+                "fp_votes_argmax": ([P, i64, i32, P, P], ctypes.c_int),
                 "fp_server_slots_in_service": ([P, ctypes.POINTER(i32)], ctypes.c_int),
                 "fp_cardinality_from_leaf_counts": ([ctypes.POINTER(fp_forest_desc), P, P], ctypes.c_int),
                 "fp_infer_cardinality": ([P, ctypes.POINTER(fp_forest_desc), P, i64, i64, P, P], ctypes.c_int),
@@ -250,6 +256,40 @@ def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_ti
     out = ctypes.c_void_p()
     _check(lib().fp_pack_forest(ctypes.byref(desc), ctypes.byref(params), ctypes.byref(out)), "fp_pack_forest")
     return PackedForest(out.value, forest)
+
+
+def fp_shard_trees(forest, bin_size: int, n_shards: int, shard: int) -> tuple[int, int]:
+    """Trees [begin, end) of one shard of a tree-bin split (whole bins,
+    balanced by expected visits)."""
+    keep: list = []
+    desc = make_desc(forest, keep)
+    b, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().fp_shard_trees(ctypes.byref(desc), bin_size, n_shards, shard, ctypes.byref(b), ctypes.byref(e)),
+           "fp_shard_trees")
+    return b.value, e.value
+
+
+def fp_pack_forest_trees(forest, tree_begin: int, tree_end: int, bin_size: int = 0, interleave_depth: int = -1,
+                         obs_tile: int = 0, warps_per_cta: int = 0, pass_bytes: int = 0, refill_lanes: int = 0,
+                         head_select: int = 0, bin_buffers: int = 0, deep_levels: int = 0) -> "PackedForest":
+    """fp_pack_forest over the trees [tree_begin, tree_end) of `forest`."""
+    keep: list = []
+    desc = make_desc(forest, keep)
+    params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes, refill_lanes,
+                            head_select, bin_buffers, deep_levels)
+    out = ctypes.c_void_p()
+    _check(lib().fp_pack_forest_trees(ctypes.byref(desc), ctypes.byref(params), tree_begin, tree_end,
+                                      ctypes.byref(out)), "fp_pack_forest_trees")
+    return PackedForest(out.value, None)
+
+
+def fp_votes_argmax(votes, out_class, stream=None) -> None:
+    """out_class[i] = the lowest class with the most votes[i] (device tensors)."""
+    T = _torch()
+    n, C = votes.shape
+    vp = _dptr(votes, T.int32, None, "votes")
+    cp = _dptr(out_class, T.int32, (n,), "out_class")
+    _check(lib().fp_votes_argmax(vp, n, C, cp, _stream_ptr(stream)), "fp_votes_argmax")
 
 
 def fp_upload(packed: "PackedForest", stream=None) -> "DeviceForest":

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libforestpack.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fp_pack.cpp", "fp_device.cu", "fp_plain.cu", "fp_probe.cu", "fp_stats.cu", "fp_server.cpp"]
+SOURCES = ["fp_pack.cpp", "fp_device.cu", "fp_plain.cu", "fp_probe.cu", "fp_stats.cu", "fp_server.cpp", "fp_shard.cu"]
 
 
 def nvcc() -> str:

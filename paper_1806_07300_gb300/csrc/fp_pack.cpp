@@ -26,6 +26,7 @@
 //        out first.
 // The image format is described in fp_internal.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -876,6 +877,101 @@ extern "C" int fp_cardinality_from_leaf_counts(const fp_forest_desc *desc, const
         return FP_OK;
     } catch (const std::bad_alloc &) {
         fp_set_error("fp_cardinality_from_leaf_counts: out of host memory");
+        return FP_ENOMEM;
+    }
+}
+
+// ------------------------------------------------- tree-bin sharding (F3)
+
+// Section III binds bins of trees to processes.  A shard is a contiguous run
+// of whole bins; the runs are cut so that each carries about the same
+// expected work.  A tree's work is its expected number of internal nodes
+// visited per observation -- the sum of its internal nodes' cardinalities over
+// the root's (the training statistics of Section III-A) -- or, without
+// cardinalities, its internal node count.
+extern "C" int fp_shard_trees(const fp_forest_desc *desc, int32_t bin_size, int32_t n_shards, int32_t shard,
+                              int32_t *tree_begin, int32_t *tree_end) {
+    if (!desc || !desc->tree_node_begin || !desc->left || !tree_begin || !tree_end || desc->n_trees < 1 ||
+        bin_size < 1 || n_shards < 1 || shard < 0 || shard >= n_shards || desc->tree_node_begin[0] != 0) {
+        fp_set_error("fp_shard_trees: bad arguments");
+        return FP_EINVAL;
+    }
+    const int32_t T = desc->n_trees;
+    const int32_t n_bins = (T + bin_size - 1) / bin_size;
+    try {
+        std::vector<double> bin_work((size_t)n_bins, 0.0);
+        for (int32_t t = 0; t < T; ++t) {
+            const int64_t b = desc->tree_node_begin[t], e = desc->tree_node_begin[t + 1];
+            if (e <= b) {
+                fp_set_error("fp_shard_trees: tree %d has no nodes", t);
+                return FP_EINVAL;
+            }
+            double w = 0.0;
+            if (desc->cardinality && desc->cardinality[b] > 0) {
+                for (int64_t v = b; v < e; ++v)
+                    if (desc->left[v] >= 0) w += (double)desc->cardinality[v];
+                w /= (double)desc->cardinality[b];
+            } else {
+                for (int64_t v = b; v < e; ++v) w += desc->left[v] >= 0 ? 1.0 : 0.0;
+            }
+            bin_work[(size_t)(t / bin_size)] += w;
+        }
+        // cut k sits at the bin boundary whose prefix of work is closest to k/n of the total
+        std::vector<double> prefix((size_t)n_bins + 1, 0.0);
+        for (int32_t b = 0; b < n_bins; ++b) prefix[(size_t)b + 1] = prefix[(size_t)b] + bin_work[(size_t)b];
+        auto cut = [&](int32_t k) -> int32_t {
+            if (k <= 0) return 0;
+            if (k >= n_shards) return n_bins;
+            const double target = prefix[(size_t)n_bins] * k / n_shards;
+            int32_t best = 0;
+            for (int32_t b = 1; b <= n_bins; ++b)
+                if (std::abs(prefix[(size_t)b] - target) < std::abs(prefix[(size_t)best] - target)) best = b;
+            return best;
+        };
+        // cuts never decrease: each is at or after the previous one
+        int32_t lo = 0, hi = 0;
+        for (int32_t k = 1; k <= shard + 1; ++k) {
+            lo = hi;
+            hi = std::max(lo, cut(k));
+        }
+        *tree_begin = std::min(T, lo * bin_size);
+        *tree_end = std::min(T, hi * bin_size);
+        return FP_OK;
+    } catch (const std::bad_alloc &) {
+        fp_set_error("fp_shard_trees: out of host memory");
+        return FP_ENOMEM;
+    }
+}
+
+// A shard's own image: the trees [tree_begin, tree_end) of desc as a forest of
+// their own (tree-local node ids, so leaf ids are unchanged).
+extern "C" int fp_pack_forest_trees(const fp_forest_desc *desc, const fp_pack_params *params, int32_t tree_begin,
+                                    int32_t tree_end, fp_packed_forest **out) {
+    if (!out || !desc || !desc->tree_node_begin || tree_begin < 0 || tree_end > desc->n_trees ||
+        tree_begin >= tree_end) {
+        if (out) *out = nullptr;
+        fp_set_error("fp_pack_forest_trees: bad arguments (trees [%d, %d) of %d)", tree_begin, tree_end,
+                     desc ? desc->n_trees : 0);
+        return FP_EINVAL;
+    }
+    try {
+        const int64_t base = desc->tree_node_begin[tree_begin];
+        std::vector<int64_t> nb((size_t)(tree_end - tree_begin) + 1);
+        for (int32_t t = tree_begin; t <= tree_end; ++t) nb[(size_t)(t - tree_begin)] = desc->tree_node_begin[t] - base;
+        fp_forest_desc sub = *desc;
+        sub.n_trees = tree_end - tree_begin;
+        sub.tree_node_begin = nb.data();
+        sub.left = desc->left ? desc->left + base : nullptr;
+        sub.right = desc->right ? desc->right + base : nullptr;
+        sub.feature = desc->feature ? desc->feature + base : nullptr;
+        sub.threshold = desc->threshold ? desc->threshold + base : nullptr;
+        sub.leaf_class = desc->leaf_class ? desc->leaf_class + base : nullptr;
+        sub.cardinality = desc->cardinality ? desc->cardinality + base : nullptr;
+        sub.leaf_value = desc->leaf_value ? desc->leaf_value + base : nullptr;
+        return fp_pack_forest(&sub, params, out);
+    } catch (const std::bad_alloc &) {
+        *out = nullptr;
+        fp_set_error("fp_pack_forest_trees: out of host memory");
         return FP_ENOMEM;
     }
 }

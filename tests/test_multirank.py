@@ -78,9 +78,25 @@ def test_profiled_traffic_lookup(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "traffic_hbm.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_fingerprint", lambda: rec["fingerprint"])
-    assert bench.profiled_traffic("hbm", params, 4000) == 20000
+    t, how = bench.profiled_traffic("hbm", params, 4000)
+    assert t == 20000 and "extrapolated" in how
+    t, how = bench.profiled_traffic("hbm", params, 1000)
+    assert t == 5000 and "extrapolated" not in how
     assert bench.profiled_entry("hbm", params)["global_load_sectors"] == 300
-    assert bench.profiled_traffic("hbm", dict(params, refill_lanes=24), 4000) is None
-    assert bench.profiled_traffic("image", params, 4000) is None
+    assert bench.profiled_traffic("hbm", dict(params, refill_lanes=24), 4000)[0] is None
+    assert bench.profiled_traffic("image", params, 4000)[0] is None
     monkeypatch.setattr(bench, "kernel_fingerprint", lambda: "0000000000000000")
-    assert bench.profiled_traffic("hbm", params, 4000) is None
+    assert bench.profiled_traffic("hbm", params, 4000)[0] is None
+
+
+def test_roofline_fraction_check():
+    """A roofline fraction far above 1 (bytes that never touch the resource)
+    stops the bench instead of being printed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.check_roofline({"frac": 0.44, "hbm": {"frac": 0.02}})
+    bench.check_roofline({"frac": 1.1, "hbm": {"frac": None}})
+    with pytest.raises(RuntimeError):
+        bench.check_roofline({"frac": 1.5})
+    with pytest.raises(RuntimeError):
+        bench.check_roofline({"frac": 0.5, "hbm": {"frac": 3.0}})
