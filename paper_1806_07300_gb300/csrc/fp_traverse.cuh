@@ -215,7 +215,7 @@ __device__ __forceinline__ void finish(const TravParams &p, uint32_t *svotes, in
         else
             report(p.status, FP_ERR_FLAG_DEVICE);
     } else if (cls < (uint32_t)p.C) {
-        atomicAdd(&svotes[r * p.C + cls], 1u);
+        atomicAdd(&svotes[cls * p.R + r], 1u);  // class-major: a burst's 32 rows hit 32 banks
     } else {
         report(p.status, FP_ERR_FLAG_DEVICE);
     }
@@ -398,7 +398,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
     const FpPass ps = p.passes[pass];
     const int nbins = ps.bin_end - ps.bin_begin;
-    const float inv_rows = 1.0f / (float)rows;
+    // task / rows as a multiply-high: with l = ceil(log2 rows) and
+    // m = floor(2^(31+l) / rows) + 1 (< 2^32), (task * m) >> (32 + l - 1) is the
+    // exact quotient for every task below 2^31 (the error m * rows - 2^(31+l)
+    // is under 2^l); tasks of a bin stay below 2048 rows * 1024 trees
+    const uint32_t div_l = rows > 1 ? 32u - (uint32_t)__clz(rows - 1) : 1u;
+    const uint32_t div_m = rows > 1 ? (uint32_t)((1ull << (31 + div_l)) / (uint64_t)rows + 1ull) : 0u;
 
     // 1. rows (feature-major, as order keys) -> shared memory; 2. the first
     //    bins' blocks in flight
@@ -453,7 +458,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
             for (int i = 0; i < nbuf && i < nbins; ++i) issue(ps.bin_begin + i, i);
     }
     if (!LEAVES)
-        for (int i = tid; i < rows * CS; i += blockDim.x) svotes[i] = 0;
+        for (int i = tid; i < R * CS; i += blockDim.x) svotes[i] = 0;
     cp_async_wait_all();
     if (D3 && !vec_rows) {  // each thread turns the values it copied into keys
         const int total = rows * F;
@@ -518,12 +523,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 }
                 const bool my = lane < ntask - base;
                 const int task = base + lane;
-                // task / rows by a float reciprocal, corrected to the exact quotient
-                int k2 = my ? (int)((float)task * inv_rows) : 0;
-                if (my) {
-                    k2 -= k2 * rows > task;
-                    k2 += (k2 + 1) * rows <= task;
-                }
+                const int k2 = !my ? 0 : (rows == 1 ? task : (int)(__umulhi((uint32_t)task, div_m) >> (div_l - 1)));
                 const int r2 = my ? task - k2 * rows : 0;
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block
@@ -552,7 +552,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                     }
                 }
                 bool busy = my && !levels;
-                while (__any_sync(0xffffffffu, busy)) {
+                while ((HK <= 0 || levels == 0) && __any_sync(0xffffffffu, busy)) {  // ranked heads only
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {  // two steps per vote
                         if (busy) {
@@ -639,24 +639,28 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     // 5. votes and class
     if (MODE == FP_MODE_VOTES && !*(volatile int *)&sh.abort) {
         if (p.n_passes == 1) {
-            if (p.out_votes) {
+            if (p.out_votes) {  // counters are class-major (svotes[c * R + r]), the output row-major
                 uint32_t *dst = p.out_votes + row0 * C;
-                for (int i = tid; i < rows * C; i += blockDim.x) dst[i] = svotes[i];
+                for (int i = tid; i < rows * C; i += blockDim.x) {
+                    const int rr = i / C;
+                    dst[i] = svotes[(i - rr * C) * R + rr];
+                }
             }
             if (p.out_class) {
                 for (int rr = tid; rr < rows; rr += blockDim.x) {
-                    const uint32_t *v = svotes + rr * C;
+                    const uint32_t *v = svotes + rr;
                     int best = 0;
                     uint32_t bv = v[0];
                     for (int c = 1; c < C; ++c)
-                        if (v[c] > bv) { bv = v[c]; best = c; }
+                        if (v[c * R] > bv) { bv = v[c * R]; best = c; }
                     p.out_class[row0 + rr] = best;
                 }
             }
         } else {
             uint32_t *dst = p.acc + row0 * C;
             for (int i = tid; i < rows * C; i += blockDim.x) {
-                const uint32_t v = svotes[i];
+                const int rr = i / C;
+                const uint32_t v = svotes[(i - rr * C) * R + rr];
                 if (v) atomicAdd(dst + i, v);
             }
             if (p.out_class) {

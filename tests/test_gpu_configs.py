@@ -65,16 +65,19 @@ def test_wide_forest_every_row(forests):
 
 def test_batched_hbm_image_wide_one_launch_graph(forests):
     """The HBM-resident forest (5 passes, three-level super-nodes, order-key
-    compares), the image forest (784 features, float compares) and the wide
-    forest in one persistent launch; captured once, replayed on two sets of
-    rows; every row compared with the oracle."""
-    names = ["hbm", "image", "wide", "tiny"]
-    sizes = [150_000, 20_011, 30_000, 4_099]
-    dfs = [fp.fp_upload(fp.fp_pack_forest(forests[k])) for k in names]
+    compares), the image forest (784 features, float compares), the wide
+    forest and a two-level packing of the HBM-resident forest in one
+    persistent launch, so both kinds of walk run in it; captured once,
+    replayed on two sets of rows; every row compared with the oracle."""
+    names = ["hbm", "image", "wide", "tiny", "hbm2"]
+    sizes = [150_000, 20_011, 30_000, 4_099, 7_777]
+    forests = dict(forests, hbm2=forests["hbm"])
+    dfs = [fp.fp_upload(fp.fp_pack_forest(forests[k], deep_levels=2 if k == "hbm2" else 0)) for k in names]
     info = {k: d.info for k, d in zip(names, dfs)}
     assert info["hbm"]["passes"] > 1 and info["hbm"]["deep_levels"] == 3
     assert info["image"]["deep_levels"] == 2 and info["wide"]["deep_levels"] == 2
-    pools = {k: datagen.test_rows(k, 2 * n)[0] for k, n in zip(names, sizes)}
+    assert info["hbm2"]["deep_levels"] == 2
+    pools = {k: datagen.test_rows(k if k != "hbm2" else "hbm", 2 * n)[0] for k, n in zip(names, sizes)}
     Xs = [torch.empty((n, forests[k].n_features), dtype=torch.float32, device="cuda") for k, n in zip(names, sizes)]
     votes = [torch.empty((n, forests[k].n_classes), dtype=torch.int32, device="cuda") for k, n in zip(names, sizes)]
     cls = [torch.empty((n,), dtype=torch.int32, device="cuda") for n in sizes]
