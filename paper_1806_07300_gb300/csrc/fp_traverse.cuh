@@ -398,12 +398,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     const int rows = (int)(p.n - row0 < (int64_t)R ? p.n - row0 : (int64_t)R);
     const FpPass ps = p.passes[pass];
     const int nbins = ps.bin_end - ps.bin_begin;
-    // task / rows as a multiply-high: with l = ceil(log2 rows) and
-    // m = floor(2^(31+l) / rows) + 1 (< 2^32), (task * m) >> (32 + l - 1) is the
-    // exact quotient for every task below 2^31 (the error m * rows - 2^(31+l)
-    // is under 2^l); tasks of a bin stay below 2048 rows * 1024 trees
-    const uint32_t div_l = rows > 1 ? 32u - (uint32_t)__clz(rows - 1) : 1u;
-    const uint32_t div_m = rows > 1 ? (uint32_t)((1ull << (31 + div_l)) / (uint64_t)rows + 1ull) : 0u;
+    const float inv_rows = 1.0f / (float)rows;
 
     // 1. rows (feature-major, as order keys) -> shared memory; 2. the first
     //    bins' blocks in flight
@@ -523,7 +518,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 }
                 const bool my = lane < ntask - base;
                 const int task = base + lane;
-                const int k2 = !my ? 0 : (rows == 1 ? task : (int)(__umulhi((uint32_t)task, div_m) >> (div_l - 1)));
+                // task / rows by a float reciprocal, corrected to the exact quotient
+                int k2 = my ? (int)((float)task * inv_rows) : 0;
+                if (my) {
+                    k2 -= k2 * rows > task;
+                    k2 += (k2 + 1) * rows <= task;
+                }
                 const int r2 = my ? task - k2 * rows : 0;
                 uint32_t hr = 0;  // head rank (or slot), then nranks + exit index
                 const uint2 *hn = hnode + k2;  // this lane's tree column of the block

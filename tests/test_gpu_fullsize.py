@@ -12,7 +12,7 @@ import pytest
 import datagen
 import oracle
 import paper_1806_07300_gb300 as fp
-from bench import HBM_LAUNCHES, HBM_LAYOUTS
+from bench import HBM_LAUNCHES, HBM_LAYOUTS, TUNE
 from paper_1806_07300_gb300 import autotune as at
 
 torch = pytest.importorskip("torch")
@@ -84,9 +84,12 @@ def test_hbm_workload_full_size(layout):
     _run("hbm", datagen.RECIPES["hbm"]["n_test"], layout, HBM_LAUNCHES)
 
 
-@pytest.mark.parametrize("layout", [None, (16, 5, 1), (2, 8, 3)])
+@pytest.mark.parametrize("layout", [None, (2, 8, 3)] + list(TUNE["image"][0]))
 def test_image_workload_full_size(layout):
-    _run("image", datagen.RECIPES["image"]["n_test"], layout)
+    """The library defaults, a ranked-head layout, and every layout and launch
+    the benchmark's tuner may pick for this workload."""
+    _run("image", datagen.RECIPES["image"]["n_test"], layout,
+         TUNE["image"][1] if layout in TUNE["image"][0] else (None,))
 
 
 def _run_values(name, layout, launch):

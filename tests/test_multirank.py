@@ -89,14 +89,19 @@ def test_profiled_traffic_lookup(tmp_path, monkeypatch):
     assert bench.profiled_traffic("hbm", params, 4000)[0] is None
 
 
-def test_roofline_fraction_check():
+def test_roofline_fraction_check(monkeypatch):
     """A roofline fraction far above 1 (bytes that never touch the resource)
-    stops the bench instead of being printed."""
+    stops the bench instead of being printed, except under a profiler."""
     sys.path.insert(0, ROOT)
     import bench
+    monkeypatch.delenv("CUDA_INJECTION64_PATH", raising=False)
     bench.check_roofline({"frac": 0.44, "hbm": {"frac": 0.02}})
     bench.check_roofline({"frac": 1.1, "hbm": {"frac": None}})
     with pytest.raises(RuntimeError):
         bench.check_roofline({"frac": 1.5})
     with pytest.raises(RuntimeError):
         bench.check_roofline({"frac": 0.5, "hbm": {"frac": 3.0}})
+    monkeypatch.setenv("CUDA_INJECTION64_PATH", "/profiler/injection.so")
+    r = {"frac": 3.0}
+    bench.check_roofline(r)
+    assert r["check"].startswith("skipped")
