@@ -407,34 +407,39 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
     {
         if (vec_rows) {
             // lane = row: 16-byte loads along the row, and each store of a
-            // warp writes 32 consecutive rows of one feature (32 banks)
+            // warp writes 32 consecutive rows of one feature (32 banks).  The
+            // work is cut into units of 32 rows x 16 features, dealt out to
+            // all warps, so that a tile of few wide rows (784 features, 64
+            // rows) is staged by every warp, not by two
             const int nq = F >> 2;
-            for (int g = warp; g * 32 < rows; g += nwarps) {
+            const int groups = (rows + 31) >> 5, qblocks = (nq + 3) >> 2;
+            for (int u = warp; u < groups * qblocks; u += nwarps) {
+                const int g = u % groups, q0 = (u / groups) * 4;
                 const int r = g * 32 + lane;
                 if (r < rows) {
                     const float4 *rp = reinterpret_cast<const float4 *>(src + (int64_t)r * F);
                     uint32_t *dst = xs + r;
-                    int q = 0;
-                    for (; q + 4 <= nq; q += 4) {
+                    if (q0 + 4 <= nq) {
                         float4 v[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) v[u] = __ldg(rp + q + u);
+                        for (int k = 0; k < 4; ++k) v[k] = __ldg(rp + q0 + k);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            uint32_t *d = dst + (4 * (q + u)) * R;
-                            d[0] = staged<D3>(v[u].x);
-                            d[R] = staged<D3>(v[u].y);
-                            d[2 * R] = staged<D3>(v[u].z);
-                            d[3 * R] = staged<D3>(v[u].w);
+                        for (int k = 0; k < 4; ++k) {
+                            uint32_t *d = dst + (4 * (q0 + k)) * R;
+                            d[0] = staged<D3>(v[k].x);
+                            d[R] = staged<D3>(v[k].y);
+                            d[2 * R] = staged<D3>(v[k].z);
+                            d[3 * R] = staged<D3>(v[k].w);
                         }
-                    }
-                    for (; q < nq; ++q) {
-                        const float4 v = __ldg(rp + q);
-                        uint32_t *d = dst + (4 * q) * R;
-                        d[0] = staged<D3>(v.x);
-                        d[R] = staged<D3>(v.y);
-                        d[2 * R] = staged<D3>(v.z);
-                        d[3 * R] = staged<D3>(v.w);
+                    } else {
+                        for (int q = q0; q < nq; ++q) {
+                            const float4 v = __ldg(rp + q);
+                            uint32_t *d = dst + (4 * q) * R;
+                            d[0] = staged<D3>(v.x);
+                            d[R] = staged<D3>(v.y);
+                            d[2 * R] = staged<D3>(v.z);
+                            d[3 * R] = staged<D3>(v.w);
+                        }
                     }
                 }
             }
@@ -451,6 +456,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         for (int i = 0; i < FP_NBUF; ++i) sh.use0[i] = sh.issued[i];
         if (!sh.abort)
             for (int i = 0; i < nbuf && i < nbins; ++i) issue(ps.bin_begin + i, i);
+
     }
     if (!LEAVES)
         for (int i = tid; i < R * CS; i += blockDim.x) svotes[i] = 0;
