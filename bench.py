@@ -69,7 +69,8 @@ WORKLOADS = {
 
 # Layout and launch candidates timed by the autotuner for the default workload
 # (the bin-size / interleaved-depth pairs that led the sweeps on this forest).
-# (B, d, head_select[, deep_levels]); without deep_levels the library's default (three levels here)
+# (B, d, head_select[, deep_levels[, deep_format]]); without deep_levels the library's default (three levels
+# here: format 1 for the hbm, regress and boosted forests, format 2 for the image forest)
 HBM_LAYOUTS = [(3, 9, 2), (4, 9, 2), (5, 9, 2), (1, 11, 2), (4, 9, 1), (3, 8, 3), (3, 9, 2, 2)]
 HBM_LAUNCHES = [(1024, 32, 16, 2), (1024, 32, 24, 2), (768, 32, 16, 2), (1024, 32, 16, 3)]  # tile, warps, refill, buffers
 # the value workloads: the regression forest's trees resemble the hbm ones; the
@@ -79,8 +80,9 @@ TUNE = {
     "regress": ([(4, 9, 2), (3, 9, 2), (4, 9, 1), (3, 8, 1)], HBM_LAUNCHES),
     # 784-feature rows (3.1 KB) fill shared memory quickly: 64-row tiles in one
     # 32-warp CTA with small heads of many trees (bins with more tasks, so fewer
-    # bin changes per task), or 32-row tiles in two 16-warp CTAs per SM
-    "image": ([(32, 3, 2), (16, 3, 2), (64, 1, 2), (128, 1, 2)],
+    # bin changes per task), or 32-row tiles in two 16-warp CTAs per SM; the
+    # library's default super-nodes (three levels, format 2) and two-level ones
+    "image": ([(32, 3, 2), (16, 3, 2), (64, 1, 2), (128, 1, 2), (32, 3, 2, 2)],
               [(64, 32, 16, 2), (64, 32, 8, 2), (64, 32, 24, 2), (32, 16, 8, 2)]),
     "boosted": ([(64, 5, 2), (32, 5, 2), (64, 5, 1), (16, 5, 1)],
                 [(768, 32, 16, 3), (1024, 32, 16, 3), (512, 16, 16, 3), (1024, 32, 32, 2)]),
@@ -108,6 +110,8 @@ def parse():
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--bin-buffers", type=int, default=0)
     ap.add_argument("--deep-levels", type=int, default=0, help="tree levels per super-node: 2, 3 (0: default)")
+    ap.add_argument("--deep-format", type=int, default=0,
+                    help="three-level super-nodes: 1 full keys first, 2 key prefixes in every slot (0: default)")
     ap.add_argument("--pass-bytes", type=int, default=0)
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of requests per offered rate")
     ap.add_argument("--no-roofline-check", action="store_true",
@@ -338,7 +342,7 @@ def tuned_forest(args, forest, X, name):
     tuning = None
     if explicit or args.no_autotune:
         params = dict(bin_size=args.bin_size, interleave_depth=args.depth, pass_bytes=args.pass_bytes,
-                      head_select=args.head_select, deep_levels=args.deep_levels)
+                      head_select=args.head_select, deep_levels=args.deep_levels, deep_format=args.deep_format)
         df = fp.fp_upload(fp.fp_pack_forest(forest, **params))
         df.configure(obs_tile=args.tile, warps_per_cta=args.warps, refill_lanes=args.refill,
                      bin_buffers=args.bin_buffers)
@@ -496,8 +500,8 @@ def run_packed(args, ws, rank, local):
     avg_launch_ms = total_ms / args.steps  # the timed region holds one launch per step and nothing else
     achieved = bytes_per_obs * n / (avg_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "obs_tile",
-                                   "warps_per_cta", "refill_lanes", "bin_buffers")}
+    params = {k: info[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels", "deep_format",
+                                   "obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")}
     traffic, traffic_how = profiled_traffic(name, params, n)
     # the sector-granular figure: 32 B per global-load sector the kernel touched
     # (ncu, same launch configuration), the practical bound beside the
@@ -688,8 +692,8 @@ def run_batched(args, ws, rank, local):
     out = base_line(args, ws, value, total_ms,
                     {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
                      "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
-                     "layout": {k: tuning[k] for k in ("bin_size", "interleave_depth", "head_select", "deep_levels",
-                                                       "launch")},
+                     "layout": {k: tuning.get(k) for k in ("bin_size", "interleave_depth", "head_select",
+                                                           "deep_levels", "deep_format", "launch")},
                      "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
     out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
                 "e2e": e2e, "roofline": roofline,

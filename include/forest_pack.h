@@ -122,12 +122,22 @@ typedef struct fp_forest_desc {
  *                     2 or 3 (0 = 3): two leave room for larger heads or
  *                     tiles, three hide copy latency better
  *   deep_levels       tree levels per 32-byte super-node below the head: 2
- *                     (full thresholds), 3 (the last level's thresholds
+ *                     (full thresholds), 3 (thresholds as order keys, some
  *                     shortened to key prefixes, ties decided by a side
- *                     table of full keys; needs 2 * ceil(log2 F) +
- *                     2 * ceil(log2 C) <= 24, classes not counted for
- *                     forests with leaf values), or 0 = default: 3 when that
- *                     sum is at most 16, else 2 */
+ *                     table of full keys; the field widths deep_format
+ *                     names must fit, classes not counted for forests with
+ *                     leaf values), or 0 = default: 3 when
+ *                     deep_format 1 or 2 fits (below, within the default
+ *                     bounds), else 2
+ *   deep_format       the fields of a three-level super-node: 1 = full keys
+ *                     for the first two levels, key prefixes for the last
+ *                     (needs 2 * ceil(log2 F) + 2 * ceil(log2 C) <= 24;
+ *                     default bound 16); 2 = key prefixes in every slot, of
+ *                     keys remapped onto the forest's own threshold range
+ *                     (needs ceil(log2 F) + 2 * ceil(log2 C) <= 24; default
+ *                     bound 20), for forests with many features or classes;
+ *                     0 = default: 1 where it fits, else 2.  Both compare
+ *                     exactly (a prefix tie is decided by the full key). */
 typedef struct fp_pack_params {
     int32_t bin_size;
     int32_t interleave_depth;
@@ -138,6 +148,7 @@ typedef struct fp_pack_params {
     int32_t head_select;
     int32_t bin_buffers;
     int32_t deep_levels;
+    int32_t deep_format;
 } fp_pack_params;
 
 typedef struct fp_packed_forest fp_packed_forest; /* host image, opaque */
@@ -161,6 +172,7 @@ typedef struct fp_packed_info {
     int32_t head_select;
     int32_t bin_buffers;
     int32_t deep_levels;      /* tree levels per super-node (2 or 3) */
+    int32_t deep_format;      /* three levels: 1 full keys first, 2 prefixes in every slot; else 0 */
 } fp_packed_info;
 
 /* Build the packed host image of a forest (Section III-A: DF-, Stat, Bin).

@@ -44,7 +44,8 @@ class fp_forest_desc(ctypes.Structure):
 class fp_pack_params(ctypes.Structure):
     _fields_ = [("bin_size", ctypes.c_int32), ("interleave_depth", ctypes.c_int32), ("obs_tile", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("pass_bytes", ctypes.c_int64), ("refill_lanes", ctypes.c_int32),
-                ("head_select", ctypes.c_int32), ("bin_buffers", ctypes.c_int32), ("deep_levels", ctypes.c_int32)]
+                ("head_select", ctypes.c_int32), ("bin_buffers", ctypes.c_int32), ("deep_levels", ctypes.c_int32),
+                ("deep_format", ctypes.c_int32)]
 
 
 class fp_packed_info(ctypes.Structure):
@@ -56,7 +57,7 @@ class fp_packed_info(ctypes.Structure):
                 ("total_bytes", ctypes.c_int64), ("parity_bytes", ctypes.c_int64),
                 ("max_head_bytes", ctypes.c_int32), ("passes", ctypes.c_int32), ("refill_lanes", ctypes.c_int32),
                 ("head_nodes", ctypes.c_int32), ("head_select", ctypes.c_int32), ("bin_buffers", ctypes.c_int32),
-                ("deep_levels", ctypes.c_int32)]
+                ("deep_levels", ctypes.c_int32), ("deep_format", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -248,11 +249,12 @@ def _hptr(t, dtype, shape=None, name="array"):
 
 def fp_pack_forest(forest, bin_size: int = 0, interleave_depth: int = -1, obs_tile: int = 0,
                    warps_per_cta: int = 0, pass_bytes: int = 0, refill_lanes: int = 0,
-                   head_select: int = 0, bin_buffers: int = 0, deep_levels: int = 0) -> "PackedForest":
+                   head_select: int = 0, bin_buffers: int = 0, deep_levels: int = 0,
+                   deep_format: int = 0) -> "PackedForest":
     keep: list = []
     desc = make_desc(forest, keep)
     params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes, refill_lanes,
-                            head_select, bin_buffers, deep_levels)
+                            head_select, bin_buffers, deep_levels, deep_format)
     out = ctypes.c_void_p()
     _check(lib().fp_pack_forest(ctypes.byref(desc), ctypes.byref(params), ctypes.byref(out)), "fp_pack_forest")
     return PackedForest(out.value, forest)
@@ -271,12 +273,13 @@ def fp_shard_trees(forest, bin_size: int, n_shards: int, shard: int) -> tuple[in
 
 def fp_pack_forest_trees(forest, tree_begin: int, tree_end: int, bin_size: int = 0, interleave_depth: int = -1,
                          obs_tile: int = 0, warps_per_cta: int = 0, pass_bytes: int = 0, refill_lanes: int = 0,
-                         head_select: int = 0, bin_buffers: int = 0, deep_levels: int = 0) -> "PackedForest":
+                         head_select: int = 0, bin_buffers: int = 0, deep_levels: int = 0,
+                         deep_format: int = 0) -> "PackedForest":
     """fp_pack_forest over the trees [tree_begin, tree_end) of `forest`."""
     keep: list = []
     desc = make_desc(forest, keep)
     params = fp_pack_params(bin_size, interleave_depth, obs_tile, warps_per_cta, pass_bytes, refill_lanes,
-                            head_select, bin_buffers, deep_levels)
+                            head_select, bin_buffers, deep_levels, deep_format)
     out = ctypes.c_void_p()
     _check(lib().fp_pack_forest_trees(ctypes.byref(desc), ctypes.byref(params), tree_begin, tree_end,
                                       ctypes.byref(out)), "fp_pack_forest_trees")

@@ -20,8 +20,8 @@ import numpy as np
 from . import FPError, fp_pack_forest, fp_predict, fp_predict_values, fp_upload
 
 _BLOCK_LIMIT = 48 * 1024  # bytes of one bin's interleaved block considered by default
-LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select", "deep_levels")
-_SEARCH_VERSION = "deep3-v7"  # cached results of an older search space are not reused
+LAYOUT_KEYS = ("bin_size", "interleave_depth", "head_select", "deep_levels", "deep_format")
+_SEARCH_VERSION = "deep3-v8"  # cached results of an older search space are not reused
 LAUNCH_KEYS = ("obs_tile", "warps_per_cta", "refill_lanes", "bin_buffers")
 
 
@@ -156,13 +156,16 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
         B, d = lay[0], lay[1]
         sel = lay[2] if len(lay) > 2 else 0  # 0: the library's default head kind
         dl = lay[3] if len(lay) > 3 else 0   # 0: the library's default super-nodes
+        fmt = lay[4] if len(lay) > 4 else 0  # 0: the library's default three-level format
         t0 = time.perf_counter()
         try:
-            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl))
+            df = fp_upload(fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl,
+                                          deep_format=fmt))
         except FPError as e:
-            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, error=str(e)))
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                              error=str(e)))
             continue
-        dl = df.info["deep_levels"]
+        dl, fmt = df.info["deep_levels"], df.info["deep_format"]
         pack_s = time.perf_counter() - t0
         for launch in (launches or candidate_launches(df.info["obs_tile"])):
             tile, warps, refill = launch[:3]
@@ -170,14 +173,16 @@ def autotune(forest, X, layouts=None, launches=None, reps: int = 3, use_cache: b
             try:
                 df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
             except FPError as e:
-                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, obs_tile=tile,
-                                  warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf, error=str(e)))
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                                  obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf,
+                                  error=str(e)))
                 continue
             ms = _time_predict(df, X, cls, reps)
             if ref is None:
                 ref = cls.clone()
             same = _same(ref, cls)
-            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, obs_tile=df.info["obs_tile"],
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                       obs_tile=df.info["obs_tile"],
                        warps_per_cta=warps, bin_buffers=nbuf,
                        refill_lanes=refill, passes=df.info["passes"], ms=ms, pack_s=pack_s, same_classes=same)
             table.append(row)
@@ -212,9 +217,12 @@ def upload_tuned(forest, X, **kw):
     return df, best
 
 
-# (B, d, head_select[, deep_levels]): with two-level super-nodes for all, every
-# forest of the launch has the same kind of super-node
-BATCHED_LAYOUTS = [(3, 9, 2), (3, 9, 2, 2), (8, 7, 2), (8, 7, 2, 2), (4, 8, 1), (16, 5, 2)]
+# (B, d, head_select[, deep_levels[, deep_format]]): with two-level super-nodes,
+# or three-level ones of format 2, for all, every forest of the launch has the
+# same kind of super-node (one walk compiled into the batched kernel); by
+# default forests of few features and classes take format 1, the others 2
+BATCHED_LAYOUTS = [(3, 9, 2), (3, 9, 2, 2), (3, 9, 2, 3, 2), (8, 7, 2), (8, 7, 2, 2), (8, 7, 2, 3, 2), (4, 8, 1),
+                   (16, 5, 2)]
 BATCHED_LAUNCHES = [(0, 32, 16, 3), (0, 32, 32, 3)]
 
 
@@ -232,11 +240,13 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
     for lay in (layouts or BATCHED_LAYOUTS):
         B, d, sel = lay[:3]
         dl = lay[3] if len(lay) > 3 else 0
+        fmt = lay[4] if len(lay) > 4 else 0
         try:
             dfs = [fp_upload(fp_pack_forest(f, bin_size=min(B, f.n_trees), interleave_depth=d, head_select=sel,
-                                            deep_levels=dl)) for f in forests]
+                                            deep_levels=dl, deep_format=fmt)) for f in forests]
         except FPError as e:
-            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, error=str(e)))
+            table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                              error=str(e)))
             continue
         for launch in (launches or BATCHED_LAUNCHES):
             tile, warps, refill, nbuf = launch
@@ -244,8 +254,8 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
                 for df in dfs:
                     df.configure(obs_tile=tile, warps_per_cta=warps, refill_lanes=refill, bin_buffers=nbuf)
             except FPError as e:
-                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, launch=launch,
-                                  error=str(e)))
+                table.append(dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                                  launch=launch, error=str(e)))
                 continue
             fp_predict_batched(dfs, Xs, votes, cls)
             torch.cuda.synchronize()
@@ -255,8 +265,8 @@ def autotune_batched(forests, Xs, layouts=None, launches=None, reps: int = 10) -
                 fp_predict_batched(dfs, Xs, votes, cls)
             b.record()
             torch.cuda.synchronize()
-            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, launch=list(launch),
-                       ms=a.elapsed_time(b) / reps)
+            row = dict(bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt,
+                       launch=list(launch), ms=a.elapsed_time(b) / reps)
             table.append(row)
             if best is None or row["ms"] < best["ms"]:
                 if best_dfs is not None and best_dfs[0] is not dfs:

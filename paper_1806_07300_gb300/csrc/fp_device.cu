@@ -90,29 +90,36 @@ size_t smem_bytes(int R, int F, int head_smem, int nbuf, int C, int warps, bool 
 }
 
 // The kernel variant for a forest and block size: its kind of super-node
-// (two or three levels), and up to 768 threads run the build for several CTAs
-// per SM (<= 42 registers), larger blocks the one-CTA build ...
-template <int MODE, bool D3, int HK>
+// (two levels, three of format 1 or 2), and up to 768 threads run the build
+// for several CTAs per SM (<= 42 registers), larger blocks the one-CTA build ...
+template <int MODE, int DK, int HK>
 void (*traverse_kernel_sized(const fp_device_forest *f))(TravParams) {
-    return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, D3, HK> : fp_traverse_kernel<MODE, 1, D3, HK>;
+    return f->threads <= 768 ? fp_traverse_kernel<MODE, 2, DK, HK> : fp_traverse_kernel<MODE, 1, DK, HK>;
 }
 
 // ... and its head kind (compiled in: 0 ranked, 1 level slots, 2 paired).
-template <int MODE, bool D3>
+template <int MODE, int DK>
 void (*traverse_kernel_deep(const fp_device_forest *f))(TravParams) {
     switch (f->hdr.head_select) {
-        case 1: return traverse_kernel_sized<MODE, D3, 1>(f);
-        case 2: return traverse_kernel_sized<MODE, D3, 2>(f);
-        default: return traverse_kernel_sized<MODE, D3, 0>(f);
+        case 1: return traverse_kernel_sized<MODE, DK, 1>(f);
+        case 2: return traverse_kernel_sized<MODE, DK, 2>(f);
+        default: return traverse_kernel_sized<MODE, DK, 0>(f);
     }
 }
 
+// The kernel's super-node kind of a packed header: 2, 3 (format 1) or 4 (format 2).
+int deep_kind(const FpImageHeader &h) { return h.deep_levels != 3 ? 2 : (h.deep_format == 2 ? 4 : 3); }
+
 template <int MODE>
 void (*traverse_kernel(const fp_device_forest *f))(TravParams) {
-    return f->hdr.deep_levels == 3 ? traverse_kernel_deep<MODE, true>(f) : traverse_kernel_deep<MODE, false>(f);
+    switch (deep_kind(f->hdr)) {
+        case 3: return traverse_kernel_deep<MODE, 3>(f);
+        case 4: return traverse_kernel_deep<MODE, 4>(f);
+        default: return traverse_kernel_deep<MODE, 2>(f);
+    }
 }
 
-// Every instance of the batched kernel: super-node kind (0 mixed, 2, 3) x
+// Every instance of the batched kernel: super-node kind (0 mixed, 2, 3, 4) x
 // head kind (-1 mixed, 0 ranked, 1, 2).
 template <int KIND>
 void add_batched(std::vector<void (*)(BatchParams)> &v) {
@@ -128,6 +135,7 @@ const std::vector<void (*)(BatchParams)> &batched_kernels() {
         add_batched<0>(k);
         add_batched<2>(k);
         add_batched<3>(k);
+        add_batched<4>(k);
         return k;
     }();
     return v;
@@ -135,7 +143,7 @@ const std::vector<void (*)(BatchParams)> &batched_kernels() {
 
 // The instance for a launch: index 4 * kind + (head kind + 1) into batched_kernels().
 void (*batched_kernel(int kind, int hk))(BatchParams) {
-    const int ki = kind == 3 ? 2 : (kind == 2 ? 1 : 0);
+    const int ki = kind >= 2 ? kind - 1 : 0;  // 0 mixed, 1 two levels, 2 format 1, 3 format 2
     return batched_kernels()[(size_t)(4 * ki + (hk + 1))];
 }
 
@@ -247,11 +255,18 @@ TravParams base_params(const fp_device_forest *f, const float *X, int64_t n) {
     p.spin_limit = f->spin_limit;
     p.stall = f->stall;
     p.n_super = h.n_super;
-    p.deep3 = h.deep_levels == 3;
-    if (p.deep3) {
+    p.deep_kind = deep_kind(h);
+    if (p.deep_kind >= 3) {
         p.fbits = (uint32_t)h.feature_bits;
         p.cbits = (uint32_t)h.class_bits;
-        p.sh2 = 2 * p.fbits + 2 * p.cbits;
+        p.sh2 = (p.deep_kind == 4 ? 1 : 2) * p.fbits + 2 * p.cbits;
+        p.klo = h.key_lo;
+        p.khi = h.key_hi;
+        p.kshl = h.key_shl;
+        p.kflag = h.key_flag;
+        p.kga = h.key_gap_a;
+        p.kgb = h.key_gap_b;
+        p.kgd = h.key_gap_d;
         p.fmask = (1u << p.fbits) - 1u;
         p.cmask = (1u << p.cbits) - 1u;
         p.vbase3 = (uint32_t)h.values3_base;
@@ -674,12 +689,12 @@ static int predict_batched_chunk(const fp_device_forest *const *forests, const f
     bp.work = reinterpret_cast<unsigned long long *>(sc);
     // one walk compiled in when every forest has the same kind of super-node,
     // and the head kind when every forest has the same one
-    int n3 = 0, hk = bp.p[0].levels;
+    int dk = bp.p[0].deep_kind, hk = bp.p[0].levels;
     for (int32_t j = 0; j < m; ++j) {
-        n3 += bp.p[j].deep3 ? 1 : 0;
+        if (bp.p[j].deep_kind != dk) dk = 0;
         if (bp.p[j].levels != hk) hk = -1;
     }
-    void (*kern)(BatchParams) = batched_kernel(n3 == m ? 3 : (n3 == 0 ? 2 : 0), hk);
+    void (*kern)(BatchParams) = batched_kernel(dk, hk);
     int per_sm = 0, sms = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);

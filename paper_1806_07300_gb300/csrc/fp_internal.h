@@ -15,8 +15,10 @@
 //                                    exit[e*stride + k]   = e-th exit of tree k
 //   deep     FpSuper[]           per tree, its super-nodes in Stat order; the
 //                                trees' regions follow one another
-//   deep_keys uint32[4] per super-node (three-level super-nodes only): the
-//                                full keys of its last level (slots 3..6)
+//   deep_keys uint32[4] or [8] per super-node (three-level super-nodes
+//                                only): the full keys of its last level (slots
+//                                3..6; format 1) or of all seven slots and a
+//                                zero (format 2)
 //   values   float[n_values]     forests with leaf values (see below)
 //   --- end of the classification part (class_bytes) ---
 //   parity blocks                per bin, int32 leaf id of each exit (or -1),
@@ -32,6 +34,30 @@
 // threshold t, x <= t (go left) exactly when key(x) <= key(t) -- a NaN x or t
 // goes right, as the float compare does -- so the kernel converts the rows
 // once when it stages them and every compare is an unsigned integer compare.
+//
+// Super-nodes of format 2 (below) compare remapped keys, which spread the
+// forest's own thresholds over the word.  First the widest run of keys that
+// holds no threshold key, between adjacent threshold keys ta < tb, is
+// collapsed to the single key ta + 1:
+//   g(k) = k - (tb - ta - 2)   for k >= tb,     g(k) = min(k, ta + 1) below
+// (key_gap_a = ta + 1, key_gap_b = tb, key_gap_d = tb - ta - 2; with no such
+// run, 0xFFFFFFFF, 0xFFFFFFFF and 0).  Then, with lo the smallest and top the
+// largest threshold key, hi = g(top) + 1 and b = the bit length of hi - lo,
+// when b <= 31
+//   V(k) = 0x80000000 | ((min(max(g(k), lo), hi) - lo) << (31 - b))
+// (key_lo = lo, key_hi = hi, key_shl = 31 - b, key_flag = 0x80000000), else
+// V(k) = g(k) (key_lo = 0, key_hi = 0xFFFFFFFF, key_shl = key_flag = 0).  g
+// is monotone, one-to-one on the threshold keys, and puts every key inside
+// the run strictly between g(ta) and g(tb); the clamp keeps keys below lo
+// (above top) below (above) every threshold; the shift is one-to-one.  So x
+// <= t exactly when V(key(x)) <= V(key(t)).  A NaN threshold and a dummy slot
+// store 0, below every V(key(x)) (remapped, every row value has the top bit
+// set), so every x goes right of them.  Rows are staged as V(key(x)) and
+// every stored threshold, in the heads too, is V(key(t)).  Short prefixes of
+// V distinguish the forest's thresholds far better than prefixes of the key,
+// whose top bits spend themselves on the sign and on exponents that no
+// threshold of the forest uses (for data of both signs, the run around zero
+// between the smallest negative and positive thresholds).
 //
 // Three kinds of head (the header's head_select, the same for every bin; 1
 // and 2 are the level heads, 3 the ranked one):
@@ -76,7 +102,8 @@
 // values3_base on, eight more per super-node (the value behind each exit).
 //
 // Super-nodes come in two kinds (the header's deep_levels), 32 bytes each
-// (one L2 sector, 32-byte aligned, one load):
+// (one L2 sector, 32-byte aligned, one load); three-level ones in two formats
+// (the header's deep_format):
 //
 // deep_levels = 2: a node v below the head together with its two children,
 // i.e. two levels of the tree resolved by one load:
@@ -91,7 +118,7 @@
 // implicit slots (slot i has children 2i+1, 2i+2; a leaf is carried down as
 // dummies, like the level heads) and eight exits (exit e is child e & 1 of
 // slot 3 + (e >> 1)) -- three levels per load.  With fb = feature_bits and
-// cb = class_bits:
+// cb = class_bits, format 1 (deep_format = 1, 2fb + 2cb <= 24):
 //   w[0..2] the full keys of slots 0..2
 //   w[3..6] slots 3..6: [fb-1:0] feature, [2fb-1:fb] the feature of slot
 //           0, 1, 2 (in w[3], w[4], w[5]; zero in w[6]), [2fb+2cb-1:2fb+cb]
@@ -107,13 +134,26 @@
 // with a key prefix, and when the prefixes are equal it decides with the full
 // key from deep_keys (a 4-byte load, for a small fraction of compares).  A
 // dummy slot has key 0 (every observation goes right of it, never a tie).
+//
+// Format 2 (deep_format = 2, fb + 2cb <= 24): every slot compares a prefix of
+// its remapped key V(t), and the feature sits beside it:
+//   w[0..2] slots 0..2: [fb-1:0] feature, [31:fb] the top 32 - fb bits of V
+//   w[3..6] slots 3..6: [fb-1:0] feature, [fb+cb-1:fb] class of the left exit,
+//           [fb+2cb-1:fb+cb] of the right one, [31:fb+2cb] the top bits of V
+//   w[7]    as in format 1
+// A staged V(key(x)) compared with the whole word decides the split wherever
+// its top bits differ from the slot's prefix; where they are equal (rare: the
+// forest's thresholds are spread over the prefix range) the slot's full V
+// from deep_keys decides.  Dummy slots and NaN thresholds store V = 0, whose
+// top bit never equals a remapped row value's.
+//
 // In a forest with leaf values exit e of super-node g names the value slot
 // values3_base + 8g + e.
 #pragma once
 #include <stdint.h>
 
 #define FP_IMAGE_MAGIC 0x4B435046u /* "FPCK" */
-#define FP_IMAGE_VERSION 6u
+#define FP_IMAGE_VERSION 7u
 
 #define FP_MAX_FEATURES 1024
 #define FP_MAX_CLASSES 512
@@ -163,7 +203,11 @@ struct FpImageHeader {
     int64_t n_values, off_values;  // leaf-value slots (0 for a classification forest)
     int32_t deep_levels;           // 2 or 3 tree levels per super-node
     int32_t feature_bits, class_bits;  // three-level super-nodes: field widths fb, cb
-    int32_t reserved0;
-    int64_t off_deep_keys;         // three-level super-nodes: full keys of the last level, 4 per super-node
+    int32_t deep_format;           // three-level super-nodes: 1 full keys in slots 0..2, 2 prefixes in all
+    int64_t off_deep_keys;         // three-level super-nodes: full keys, 4 (format 1) or 8 per super-node
     int64_t values3_base;          // forests with leaf values: first slot of the per-exit values
+    uint32_t key_lo, key_hi;       // format 2: the key remap V (above); identity: 0, 0xFFFFFFFF
+    uint32_t key_shl, key_flag;
+    uint32_t key_gap_a, key_gap_b;  // format 2: the collapsed run of keys (none: 0xFFFFFFFF twice)
+    uint32_t key_gap_d, reserved1;
 };

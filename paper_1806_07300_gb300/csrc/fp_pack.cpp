@@ -82,6 +82,74 @@ uint32_t thr_word(float t, bool keys) {
     return u;
 }
 
+// How a forest stores its thresholds: float bits (two-level super-nodes),
+// order keys (three-level, format 1) or remapped order keys V (format 2; the
+// map is in fp_internal.h).
+struct KeyMap {
+    int kind = 0;  // 0 float bits, 1 keys, 2 remapped keys
+    uint32_t lo = 0, hi = 0xFFFFFFFFu, shl = 0, flag = 0;
+    uint32_t ga = 0xFFFFFFFFu, gb = 0xFFFFFFFFu, gd = 0;  // the collapsed run of keys
+
+    uint32_t gap(uint32_t k) const { return k >= gb ? k - gd : std::min(k, ga); }
+    // V of an order key
+    uint32_t remap(uint32_t k) const {
+        const uint32_t g = gap(k);
+        const uint32_t c = g < lo ? lo : (g > hi ? hi : g);
+        return flag | ((c - lo) << shl);
+    }
+    uint32_t word(float t) const {
+        if (kind == 0) {
+            uint32_t u;
+            memcpy(&u, &t, 4);
+            return u;
+        }
+        const uint32_t k = thr_key(t);
+        return (kind == 1 || k == 0) ? k : remap(k);  // a NaN threshold stays 0
+    }
+};
+
+// The remap of format 2 over the thresholds of every internal node of the
+// forest: the widest run of keys without a threshold collapsed, then [lo, hi]
+// spread over 31 bits below a set top bit, or left as they are when that
+// range needs 32 bits.
+KeyMap make_remap(const fp_forest_desc *desc) {
+    KeyMap km;
+    km.kind = 2;
+    std::vector<uint32_t> keys;
+    const int64_t m = desc->tree_node_begin[desc->n_trees];
+    for (int64_t v = 0; v < m; ++v) {
+        if (desc->left[v] < 0) continue;
+        const uint32_t k = thr_key(desc->threshold[v]);
+        if (k != 0) keys.push_back(k);  // 0: NaN
+    }
+    if (keys.empty()) keys.push_back(0x80000000u);  // no thresholds
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    uint32_t best = 0;
+    size_t at = 0;
+    for (size_t i = 1; i < keys.size(); ++i)
+        if (keys[i] - keys[i - 1] > best) {
+            best = keys[i] - keys[i - 1];
+            at = i;
+        }
+    if (best > 2) {  // a run of at least two keys between adjacent thresholds
+        km.ga = keys[at - 1] + 1;
+        km.gb = keys[at];
+        km.gd = keys[at] - keys[at - 1] - 2;
+    }
+    const uint32_t lo = keys.front(), top = km.gap(keys.back());
+    const uint64_t range = (uint64_t)top + 1 - lo;
+    int32_t b = 0;
+    while (b < 64 && (range >> b) != 0) ++b;
+    if (b <= 31) {
+        km.lo = lo;
+        km.hi = top + 1;  // top is at most the key of +inf, so no wrap
+        km.shl = (uint32_t)(31 - b);
+        km.flag = 0x80000000u;
+    }
+    return km;
+}
+
 // bits that hold the values 0 .. n-1 (at least 1)
 int32_t bits_for(int32_t n) {
     int32_t b = 1;
@@ -428,6 +496,37 @@ void encode_super3(const TreeRef &t, const TreeLayout &lay, int32_t v, int32_t f
     sn.w[7] = (mask << 24) | (first ? (uint32_t)(first - lay.sn_index[v]) : 0u);
 }
 
+// A three-level super-node of format 2 (fp_internal.h): every slot holds its
+// feature beside the top bits of its remapped key (and a last-level slot its
+// exits' classes between them); the seven full keys, the leaf ids and the
+// exits' values go to side tables.
+void encode_super3p(const TreeRef &t, const TreeLayout &lay, int32_t v, int32_t fb, int32_t cb, const KeyMap &km,
+                    const float *leaf_value, FpSuper &sn, uint32_t keys[8], int32_t leaf_ids[8], float *vals) {
+    int32_t sl[7], e[8];
+    slots3(t, v, sl, e);
+    for (int i = 0; i < 7; ++i) {
+        const int32_t u = sl[i];
+        const uint32_t key = t.leaf(u) ? 0u : km.word(t.Th[u]);
+        const uint32_t low = i < 3 ? (uint32_t)fb : (uint32_t)(fb + 2 * cb);  // bits below the prefix
+        keys[i] = key;
+        sn.w[i] = (key & ~((1u << low) - 1u)) | (t.leaf(u) ? 0u : (uint32_t)t.Fe[u]);
+    }
+    keys[7] = 0;
+    uint32_t mask = 0;
+    for (int q = 0; q < 8; ++q) {
+        const int32_t c = e[q];
+        leaf_ids[q] = -1;
+        if (vals) vals[q] = 0.0f;
+        if (!t.leaf(c)) continue;
+        mask |= 1u << q;
+        leaf_ids[q] = c;
+        if (cb) sn.w[3 + q / 2] |= (uint32_t)t.Cl[c] << (fb + cb * (q & 1));
+        if (vals) vals[q] = leaf_value[c];
+    }
+    const int32_t first = lay.sn_first[lay.sn_index[v]];
+    sn.w[7] = (mask << 24) | (first ? (uint32_t)(first - lay.sn_index[v]) : 0u);
+}
+
 }  // namespace
 
 extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *params, fp_packed_forest **out) {
@@ -451,7 +550,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         fp_set_error("fp_pack_forest: tree_node_begin[0] must be 0");
         return FP_EINVAL;
     }
-    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0, 0, 0};
+    fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0, 0, 0, 0};
     const int32_t refill = p.refill_lanes ? p.refill_lanes : 32;
     int32_t B = p.bin_size ? p.bin_size : 3;
     const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
@@ -460,9 +559,20 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
     const bool select_levels = kind == 1 || kind == 2;  // level heads: single or paired slots
     const bool paired = kind == 2;
-    // three-level super-nodes: feature and class fields beside the key prefixes
+    // three-level super-nodes: feature and class fields beside the key
+    // prefixes; format 1 keeps full keys in its first two levels (two feature
+    // fields in each last-level word), format 2 prefixes in every slot
     const int32_t fb = bits_for(F), cb = desc->leaf_value ? 0 : (C > 1 ? bits_for(C) : 0);
-    const bool three = p.deep_levels == 3 || (p.deep_levels == 0 && 2 * fb + 2 * cb <= 16);
+    const bool fit1 = 2 * fb + 2 * cb <= 24, fit2 = fb + 2 * cb <= 24;
+    const bool auto1 = 2 * fb + 2 * cb <= 16, auto2 = fb + 2 * cb <= 20;  // default bounds
+    int32_t fmt = 0;  // 0: two-level super-nodes
+    if (p.deep_levels == 3)
+        fmt = p.deep_format ? p.deep_format : (fit1 ? 1 : 2);
+    else if (p.deep_levels == 0)
+        fmt = p.deep_format == 1 ? (auto1 ? 1 : 0)
+              : p.deep_format == 2 ? (auto2 ? 2 : 0)
+                                   : (auto1 ? 1 : (auto2 ? 2 : 0));
+    const bool three = fmt != 0;
     int32_t R = p.obs_tile;
     if (R == 0) {  // rows take up to ~96 KiB of shared memory
         int64_t r = (96 * 1024) / ((int64_t)F * 4);
@@ -474,15 +584,16 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         R < 32 || R > 2048 || R % 32 ||
         refill < 1 || refill > 32 || p.head_select < 0 || p.head_select > 3 || (paired && d % 2 == 0) ||
         (p.bin_buffers != 0 && p.bin_buffers != 2 && p.bin_buffers != 3) ||
-        (p.deep_levels != 0 && p.deep_levels != 2 && p.deep_levels != 3)) {
+        (p.deep_levels != 0 && p.deep_levels != 2 && p.deep_levels != 3) || p.deep_format < 0 ||
+        p.deep_format > 2) {
         fp_set_error("fp_pack_forest: bad params (bin_size %d, interleave_depth %d, obs_tile %d, warps %d, "
-                     "refill %d, head_select %d, bin_buffers %d, deep_levels %d)", B, d, R, W, refill,
-                     p.head_select, p.bin_buffers, p.deep_levels);
+                     "refill %d, head_select %d, bin_buffers %d, deep_levels %d, deep_format %d)", B, d, R, W,
+                     refill, p.head_select, p.bin_buffers, p.deep_levels, p.deep_format);
         return FP_EINVAL;
     }
-    if (three && 2 * fb + 2 * cb > 24) {
-        fp_set_error("fp_pack_forest: %d features and %d classes leave three-level super-nodes too few key bits; "
-                     "use deep_levels = 2", F, C);
+    if ((fmt == 1 && !fit1) || (fmt == 2 && !fit2)) {
+        fp_set_error("fp_pack_forest: %d features and %d classes leave three-level super-nodes of format %d too "
+                     "few key bits; use deep_format = 2 or deep_levels = 2", F, C, fmt);
         return FP_EUNSUPPORTED;
     }
     if (B > T) B = T;
@@ -530,6 +641,11 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 }
             }
         }
+
+        // how thresholds are stored (in the heads too)
+        KeyMap km;
+        if (fmt == 2) km = make_remap(desc);
+        else km.kind = three ? 1 : 0;
 
         // ---- section sizes
         FpImageHeader h;
@@ -626,7 +742,15 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.deep_levels = three ? 3 : 2;
         h.feature_bits = three ? fb : 0;
         h.class_bits = three ? cb : 0;
-        h.off_deep_keys = off; off = align_up(off + (three ? 16 * n_deep : 0), 256);
+        h.deep_format = fmt;
+        h.key_lo = km.lo;
+        h.key_hi = km.hi;
+        h.key_shl = km.shl;
+        h.key_flag = km.flag;
+        h.key_gap_a = km.ga;
+        h.key_gap_b = km.gb;
+        h.key_gap_d = km.gd;
+        h.off_deep_keys = off; off = align_up(off + (three ? (fmt == 2 ? 32 : 16) * n_deep : 0), 256);
         h.n_values = n_values;
         h.values3_base = values3_base;
         h.off_values = off; off = align_up(off + 4 * n_values, 256);
@@ -674,7 +798,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                             uint32_t w[4] = {0, 0, 0, 0};
                             for (int c = 0; c < 3; ++c) {
                                 if (tr.leaf(vv[c])) continue;  // dummy: any outcome lands on the same leaf
-                                w[c] = thr_word(tr.Th[vv[c]], three);
+                                w[c] = km.word(tr.Th[vv[c]]);
                                 w[3] |= (uint32_t)tr.Fe[vv[c]] << (10 * c);
                             }
                             memcpy(blk + (q * bn.stride + k) * 16, w, 16);
@@ -690,7 +814,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                 if (select_levels) {
                     for (size_t s = 0; s < lay.slot.size(); ++s) {
                         const int32_t v = lay.slot[s];
-                        const uint32_t thr = tr.leaf(v) ? 0u : thr_word(tr.Th[v], three);
+                        const uint32_t thr = tr.leaf(v) ? 0u : km.word(tr.Th[v]);
                         const uint32_t meta = tr.leaf(v) ? 0u : (uint32_t)tr.Fe[v] << 22;
                         uint8_t *rec = blk + ((int64_t)s * bn.stride + k) * 8;
                         memcpy(rec, &thr, 4);
@@ -713,7 +837,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                         tgt[0] = tgt[1] = (uint32_t)bn.nranks;
                         meta = 0;
                     } else {
-                        thr = thr_word(tr.Th[v], three);
+                        thr = km.word(tr.Th[v]);
                         meta = (uint32_t)tr.Fe[v] << 22;
                         const int32_t c2[2] = {tr.L[v], tr.R[v]};
                         for (int s2 = 0; s2 < 2; ++s2) {
@@ -758,12 +882,15 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
             for (size_t i = 0; i < lay.sn_root.size(); ++i) {
                 const int64_t g = tree_base[t] + (int64_t)i;
                 if (three) {
-                    uint32_t *keys = reinterpret_cast<uint32_t *>(img + h.off_deep_keys) + 4 * g;
                     float *vals = desc->leaf_value
                                       ? reinterpret_cast<float *>(img + h.off_values) + values3_base + 8 * g
                                       : nullptr;
-                    encode_super3(tr, lay, lay.sn_root[i], fb, cb, desc->leaf_value ? desc->leaf_value + nb : nullptr,
-                                  deep[g], keys, dleaf + 8 * g, vals);
+                    const float *lv = desc->leaf_value ? desc->leaf_value + nb : nullptr;
+                    uint32_t *keys = reinterpret_cast<uint32_t *>(img + h.off_deep_keys) + (fmt == 2 ? 8 : 4) * g;
+                    if (fmt == 2)
+                        encode_super3p(tr, lay, lay.sn_root[i], fb, cb, km, lv, deep[g], keys, dleaf + 8 * g, vals);
+                    else
+                        encode_super3(tr, lay, lay.sn_root[i], fb, cb, lv, deep[g], keys, dleaf + 8 * g, vals);
                 } else {
                     encode_super(tr, lay, lay.sn_root[i], tree_base[t], deep[g], dleaf + 4 * g);
                 }
@@ -812,6 +939,7 @@ void fp_fill_info(const FpImageHeader *h, fp_packed_info *info) {
     info->refill_lanes = h->refill_lanes;
     info->bin_buffers = h->bin_buffers;
     info->deep_levels = h->deep_levels;
+    info->deep_format = h->deep_format;
 }
 
 extern "C" const void *fp_packed_image(const fp_packed_forest *pf, int64_t *bytes) {

@@ -90,11 +90,14 @@ struct TravParams {
     float *acc_val;           // values mode, several passes: per-row accumulator
     int32_t spin_limit;       // polls of a bin block's barrier before the wait gives up
     int32_t stall;            // fault injection: bin waits ignore completed copies (0 normally)
-    int32_t deep3;            // super-nodes of three levels (else two)
-    uint32_t fbits, sh2;      // three levels: feature bits; key-prefix shift of the last level (2fb + 2cb)
+    int32_t deep_kind;        // super-nodes: 2 two levels, 3 three levels (format 1), 4 three levels (format 2)
+    uint32_t fbits, sh2;      // three levels: feature bits; key-prefix shift of the last level
+                              // (2fb + 2cb in format 1, fb + 2cb in format 2)
     uint32_t cbits, fmask, cmask;  // three levels: class bits, feature and class masks
     uint32_t vbase3;          // three levels, values mode: first per-exit value slot
-    const uint32_t *deep_keys;  // three levels: full keys of the last level, 4 per super-node
+    const uint32_t *deep_keys;  // three levels: full keys, 4 (format 1) or 8 (format 2) per super-node
+    uint32_t klo, khi, kshl, kflag;  // format 2: the key remap V of the staged rows
+    uint32_t kga, kgb, kgd;          // format 2: its collapsed run of keys
     int64_t n_super;
 };
 
@@ -148,11 +151,19 @@ __device__ __forceinline__ uint32_t obs_key(float v) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// A staged observation value: its order key (KEYS, forests with three-level
-// super-nodes) or its float bits.
-template <bool KEYS>
-__device__ __forceinline__ uint32_t staged(float v) {
-    return KEYS ? obs_key(v) : __float_as_uint(v);
+// The remapped key V of format 2 (fp_internal.h): the run of keys without a
+// threshold collapsed, then clamped to the forest's threshold range and
+// spread over the 31 bits below a set top bit.
+__device__ __forceinline__ uint32_t remap_key(const TravParams &p, uint32_t k) {
+    const uint32_t g = k >= p.kgb ? k - p.kgd : min(k, p.kga);
+    return p.kflag | ((min(max(g, p.klo), p.khi) - p.klo) << p.kshl);
+}
+
+// A staged observation value for super-node kind DK: its float bits (2), its
+// order key (3) or its remapped key (4).
+template <int DK>
+__device__ __forceinline__ uint32_t staged(const TravParams &p, float v) {
+    return DK == 2 ? __float_as_uint(v) : (DK == 3 ? obs_key(v) : remap_key(p, obs_key(v)));
 }
 
 // x <= t, the split's test (go left): keys compare as unsigned integers,
@@ -284,13 +295,67 @@ __device__ __forceinline__ void deep_finish3(const TravParams &p, const uint32_t
     }
 }
 
-// D3: the forest's super-nodes have three levels (p.deep3), else two; a
-// compile-time choice, so neither kind's step carries the other's code.
-template <int MODE, bool D3>
+// Three levels, format 2: every slot's word is the top bits of its remapped
+// key over its feature (and classes), so comparing the staged V with the
+// whole word decides the split wherever their top bits differ.  Where they
+// are equal for any of the three slots of the walk (rare), the step is taken
+// again with the slots' full keys from the side table.
+template <int MODE>
+__device__ __forceinline__ void deep_finish3p(const TravParams &p, const uint32_t *xs, uint32_t *svotes,
+                                              int64_t row0, LaneTask &L, const uint32_t w[8]) {
+    const uint32_t *xr = xs + L.r;
+    const int R = p.R;
+    const uint32_t fm = p.fmask, fb = p.fbits, s2 = p.sh2;
+    const uint32_t k0 = xr[(w[0] & fm) * R];
+    uint32_t d0 = k0 > w[0] ? 1u : 0u;
+    uint32_t n1 = d0 ? w[2] : w[1];
+    const uint32_t k1 = xr[(n1 & fm) * R];
+    uint32_t d1 = k1 > n1 ? 1u : 0u;
+    uint32_t j = 2 * d0 + d1;  // last-level slot 3 + j
+    uint32_t n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
+    uint32_t k2 = xr[(n2 & fm) * R];
+    uint32_t d2 = k2 > n2 ? 1u : 0u;
+    if ((min(k0 ^ w[0], k1 ^ n1) >> fb) == 0u || ((k2 ^ n2) >> s2) == 0u) {
+        const uint32_t *fk = p.deep_keys + 8 * (int64_t)L.ref;
+        d0 = k0 > __ldg(fk) ? 1u : 0u;
+        n1 = d0 ? w[2] : w[1];
+        d1 = xr[(n1 & fm) * R] > __ldg(fk + 1 + d0) ? 1u : 0u;
+        j = 2 * d0 + d1;
+        n2 = d0 ? (d1 ? w[6] : w[5]) : (d1 ? w[4] : w[3]);
+        k2 = xr[(n2 & fm) * R];
+        d2 = k2 > __ldg(fk + 3 + j) ? 1u : 0u;
+    }
+    const uint32_t e = 2 * j + d2;
+    const uint32_t mask = w[7] >> 24;
+    if ((mask >> e) & 1u) {
+        L.active = false;
+        int32_t leaf_id = -1;
+        if (MODE == FP_MODE_LEAVES) leaf_id = p.deep_leaf[8 * (int64_t)L.ref + e];
+        const uint32_t cls =
+            MODE == FP_MODE_VALUES ? p.vbase3 + 8 * L.ref + e : (n2 >> (fb + p.cbits * d2)) & p.cmask;
+        finish<MODE>(p, svotes, row0, L.r, L.t, cls, leaf_id);
+    } else {
+        const uint32_t nref = L.ref + (w[7] & FP_DEEP3_OFFSET_MASK) + __popc(~mask & ((1u << e) - 1u));
+        if (nref > L.ref && (int64_t)nref < p.n_super) {  // forward only, so every walk ends
+            L.ref = nref;
+        } else {
+            report(p.status, FP_ERR_FLAG_DEVICE);
+            L.active = false;
+        }
+    }
+}
+
+// DK: the forest's kind of super-node (p.deep_kind: 2, 3 or 4); a
+// compile-time choice, so no kind's step carries another's code.
+template <int MODE, int DK>
 __device__ __forceinline__ void deep_finish(const TravParams &p, const uint32_t *xs, uint32_t *svotes, int64_t row0,
                                             LaneTask &L, const uint32_t w[8]) {
-    if (D3) {
+    if (DK == 3) {
         deep_finish3<MODE>(p, xs, svotes, row0, L, w);
+        return;
+    }
+    if (DK == 4) {
+        deep_finish3p<MODE>(p, xs, svotes, row0, L, w);
         return;
     }
     const int R = p.R;
@@ -359,12 +424,13 @@ __device__ __forceinline__ void cta_finish(CtaShared &sh) {
 // HK: the head kind when known at compile time (0 ranked, 1 level slots,
 // 2 paired level slots), or -1 to read it from p.levels (the batched kernel,
 // whose forests may differ).
-template <int MODE, bool D3, int HK>
+template <int MODE, int DK, int HK>
 __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint8_t *smem, CtaShared &sh) {
+    constexpr bool D3 = DK >= 3;  // rows and thresholds are (remapped) order keys
     constexpr bool LEAVES = MODE == FP_MODE_LEAVES, VALUES = MODE == FP_MODE_VALUES;
     const int levels = HK >= 0 ? HK : p.levels;
     const int R = p.R, F = p.F, C = p.C;
-    uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // the tile's rows: order keys (D3) or float bits
+    uint32_t *xs = reinterpret_cast<uint32_t *>(smem);  // the tile's rows: (remapped) order keys or float bits
     const int xs_bytes = ((F * R * 4) + 15) & ~15;
     const int nbuf = p.nbuf;
     uint8_t *const hbuf0 = smem + xs_bytes;  // nbuf bin-block buffers, head_smem bytes each
@@ -426,19 +492,19 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             uint32_t *d = dst + (4 * (q0 + k)) * R;
-                            d[0] = staged<D3>(v[k].x);
-                            d[R] = staged<D3>(v[k].y);
-                            d[2 * R] = staged<D3>(v[k].z);
-                            d[3 * R] = staged<D3>(v[k].w);
+                            d[0] = staged<DK>(p, v[k].x);
+                            d[R] = staged<DK>(p, v[k].y);
+                            d[2 * R] = staged<DK>(p, v[k].z);
+                            d[3 * R] = staged<DK>(p, v[k].w);
                         }
                     } else {
                         for (int q = q0; q < nq; ++q) {
                             const float4 v = __ldg(rp + q);
                             uint32_t *d = dst + (4 * q) * R;
-                            d[0] = staged<D3>(v.x);
-                            d[R] = staged<D3>(v.y);
-                            d[2 * R] = staged<D3>(v.z);
-                            d[3 * R] = staged<D3>(v.w);
+                            d[0] = staged<DK>(p, v.x);
+                            d[R] = staged<DK>(p, v.y);
+                            d[2 * R] = staged<DK>(p, v.z);
+                            d[3 * R] = staged<DK>(p, v.w);
                         }
                     }
                 }
@@ -466,7 +532,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         for (int e = tid; e < total; e += blockDim.x) {
             const int r = e / F;
             uint32_t *x = xs + (e - r * F) * R + r;
-            *x = obs_key(__uint_as_float(*x));
+            *x = staged<DK>(p, __uint_as_float(*x));
         }
     }
     __syncthreads();
@@ -518,7 +584,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 if (lane == 0) base = atomicAdd(&sh.task_next[buf], 32);
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= ntask) {  // the bin is claimed out: use the load in flight, then move on
-                    if (L.active) deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
+                    if (L.active) deep_finish<MODE, DK>(p, xs, svotes, row0, L, w);
                     pop_tasks(p, ring, head, tail, L, lt_mask);
                     break;
                 }
@@ -593,7 +659,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
                 tail += __popc(pm);
                 __syncwarp();
             }
-            if (L.active) deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
+            if (L.active) deep_finish<MODE, DK>(p, xs, svotes, row0, L, w);
             pop_tasks(p, ring, head, tail, L, lt_mask);
         }
         // this warp reads the bin's block no more; the last warp refills the buffer
@@ -614,7 +680,7 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
         if (L.active) {
             uint32_t w[8];
             deep_issue(p, L, w);
-            deep_finish<MODE, D3>(p, xs, svotes, row0, L, w);
+            deep_finish<MODE, DK>(p, xs, svotes, row0, L, w);
         }
     }
     __syncthreads();
@@ -698,12 +764,12 @@ __device__ __forceinline__ void run_item(const TravParams &p, int64_t item, uint
 // MINB = 2: CTAs of up to 768 threads, at most 42 registers a thread, so that
 // two 24-warp or three 16-warp CTAs share an SM when shared memory allows:
 // more warps to hide the latency of the dependent loads of each walk.
-template <int MODE, int MINB, bool D3, int HK>
+template <int MODE, int MINB, int DK, int HK>
 __global__ void __launch_bounds__(MINB == 1 ? 1024 : 768, MINB) fp_traverse_kernel(const TravParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ CtaShared sh;
     cta_init(sh);
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE, D3, HK>(p, item, smem, sh);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) run_item<MODE, DK, HK>(p, item, smem, sh);
     cta_finish(sh);
 }
 
@@ -719,8 +785,8 @@ struct BatchParams {
     unsigned long long *work;  // zeroed before the launch
 };
 
-// KIND: 2 or 3 when every forest of the launch has super-nodes of that many
-// levels (one walk compiled in), 0 for a mix (both, chosen per item).  HK:
+// KIND: 2, 3 or 4 when every forest of the launch has that kind of
+// super-node (one walk compiled in), 0 for a mix (all, chosen per item).  HK:
 // the head kind when all forests share it (0 ranked, 1, 2), else -1.
 template <int KIND, int HK>
 __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __grid_constant__ BatchParams bp) {
@@ -736,10 +802,12 @@ __global__ void __launch_bounds__(1024, 1) fp_traverse_batched_kernel(const __gr
         if (item >= total) break;
         int j = 0;
         while (j + 1 < bp.k && bp.item_begin[j + 1] <= item) ++j;
-        if (KIND == 3 || (KIND == 0 && bp.p[j].deep3))
-            run_item<FP_MODE_VOTES, true, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
+        if (KIND == 3 || (KIND == 0 && bp.p[j].deep_kind == 3))
+            run_item<FP_MODE_VOTES, 3, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
+        else if (KIND == 4 || (KIND == 0 && bp.p[j].deep_kind == 4))
+            run_item<FP_MODE_VOTES, 4, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
         else
-            run_item<FP_MODE_VOTES, false, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
+            run_item<FP_MODE_VOTES, 2, HK>(bp.p[j], item - bp.item_begin[j], smem, sh);
     }
     cta_finish(sh);
 }

@@ -13,7 +13,9 @@ HDR = np.dtype([("magic", "<u4"), ("version", "<u4"), ("n_trees", "<i4"), ("n_fe
                 ("off_deep", "<i8"), ("off_pheads", "<i8"), ("off_deep_leaf", "<i8"), ("class_bytes", "<i8"),
                 ("total_bytes", "<i8"), ("head_bytes_total", "<i8"), ("pass_bytes", "<i8"), ("n_internal", "<i8"),
                 ("n_values", "<i8"), ("off_values", "<i8"), ("deep_levels", "<i4"), ("feature_bits", "<i4"),
-                ("class_bits", "<i4"), ("reserved0", "<i4"), ("off_deep_keys", "<i8"), ("values3_base", "<i8")],
+                ("class_bits", "<i4"), ("deep_format", "<i4"), ("off_deep_keys", "<i8"), ("values3_base", "<i8"),
+                ("key_lo", "<u4"), ("key_hi", "<u4"), ("key_shl", "<u4"), ("key_flag", "<u4"),
+                ("key_gap_a", "<u4"), ("key_gap_b", "<u4"), ("key_gap_d", "<u4"), ("reserved1", "<u4")],
                align=True)
 BIN = np.dtype([("head_off", "<u4"), ("head_bytes", "<u4"), ("first_tree", "<i4"), ("width", "<i4"),
                 ("phead_off", "<u4"), ("stride", "<i4"), ("nranks", "<i4"), ("nexits", "<i4")])
@@ -59,14 +61,17 @@ class Image:
         deep = img[g["off_deep"]: g["off_deep"] + 32 * g["n_super"]]
         self.sw = deep.view("<u4").reshape(-1, 8)          # super-node words
         self.sthr = deep.view("<f4").reshape(-1, 8)[:, :3]  # two levels: thresholds of v, left, right
-        # thresholds are order keys with three-level super-nodes, else floats
+        # thresholds are order keys with three-level super-nodes (remapped
+        # ones in format 2), else floats
         self.keys = g["deep_levels"] == 3
+        self.fmt = g["deep_format"] if self.keys else 0
         ne = 8 if g["deep_levels"] == 3 else 4
         dl = img[g["off_deep_leaf"]: g["off_deep_leaf"] + 4 * ne * g["n_super"]].view("<i4")
         self.deep_leaf = dl.reshape(-1, ne)
         if g["deep_levels"] == 3:
-            dk = img[g["off_deep_keys"]: g["off_deep_keys"] + 16 * g["n_super"]].view("<u4")
-            self.deep_keys = dk.reshape(-1, 4)  # full keys of slots 3..6
+            nk = 8 if self.fmt == 2 else 4
+            dk = img[g["off_deep_keys"]: g["off_deep_keys"] + 4 * nk * g["n_super"]].view("<u4")
+            self.deep_keys = dk.reshape(-1, nk)  # full keys of slots 3..6 (format 1) or 0..6 (format 2)
         self.ties = 0  # three levels: compares decided by the full keys in the last walk
         # forests with leaf values: a leaf reference names a slot of this table
         self.values = img[g["off_values"]: g["off_values"] + 4 * g["n_values"]].view("<f4")
@@ -93,16 +98,38 @@ class Image:
         par = self.img[pb: pb + 4 * ne * st].view("<i4").reshape(ne, st)
         return thr, meta, exits, par
 
+    def remap(self, k) -> np.ndarray:
+        """The format-2 map V of order keys: the run of keys from key_gap_a
+        to key_gap_b collapsed onto key_gap_a (keys from key_gap_b up move
+        down by key_gap_d), then clamped to [key_lo, key_hi] and shifted up
+        by key_shl below key_flag."""
+        g = self.h
+        k = np.asarray(k, np.int64)
+        k = np.where(k >= g["key_gap_b"], k - g["key_gap_d"], np.minimum(k, g["key_gap_a"]))
+        c = np.clip(k, g["key_lo"], g["key_hi"]) - g["key_lo"]
+        return ((c << g["key_shl"]) | g["key_flag"]).astype(np.int64) & 0xFFFFFFFF
+
     def word(self, t) -> np.ndarray:
-        """A threshold as the image stores it: its key, or its float bits."""
-        return thr_key(t) if self.keys else np.array(t, dtype=np.float32).view(np.uint32)
+        """A threshold as the image stores it: its key (remapped in format 2;
+        a NaN threshold stays 0), or its float bits."""
+        if not self.keys:
+            return np.array(t, dtype=np.float32).view(np.uint32)
+        k = thr_key(t)
+        if self.fmt == 2:
+            k = np.where(k == 0, 0, self.remap(k)).astype(np.uint32)
+        return k
 
     def walk(self, X: np.ndarray):
         """Leaf id and class (or value slot) per (observation, tree), decoding
         the records; X holds float observations, compared through their keys
         when the image stores keys."""
         g = self.h
-        X = obs_key(X).astype(np.int64) if self.keys else np.asarray(X, dtype=np.float32)
+        if self.keys:
+            X = obs_key(X).astype(np.int64)
+            if self.fmt == 2:
+                X = self.remap(X)
+        else:
+            X = np.asarray(X, dtype=np.float32)
         self.ties = 0
         n, T = X.shape[0], g["n_trees"]
         leaf = np.full((n, T), -2, np.int32)
@@ -150,7 +177,8 @@ class Image:
                     a = rows[state == 1]
                     g_idx = idx[a]
                     if g["deep_levels"] == 3:
-                        ex, nref, c3 = self._step3(X, a, g_idx)
+                        step = self._step3p if self.fmt == 2 else self._step3
+                        ex, nref, c3 = step(X, a, g_idx)
                         fin = (nref & LEAF) != 0
                         fa = a[fin]
                         cls[fa, t] = c3[fin]
@@ -205,4 +233,43 @@ class Image:
             c3 = g["values3_base"] + 8 * g_idx.astype(np.int64) + ex
         else:
             c3 = (n2 >> (2 * fb + cb * e2.astype(np.int64))) & ((1 << cb) - 1)
+        return ex, nref, c3.astype(np.int32)
+
+    def _step3p(self, X, a, g_idx):
+        """One three-level super-node of format 2 per row of a: every slot's
+        word holds the top bits of its remapped key over its feature (and, in
+        the last level, the exits' classes).  The walk follows the full keys
+        of the side table; every compare where the row's top bits differ from
+        the slot's must agree with the word compare, and the others (ties)
+        are counted."""
+        g = self.h
+        fb, cb = g["feature_bits"], g["class_bits"]
+        fm = (1 << fb) - 1
+        w = self.sw[g_idx].astype(np.int64)
+        K = self.deep_keys[g_idx].astype(np.int64)
+        ar = np.arange(len(a))
+
+        def decide(slot_word, full, low):
+            x = X[a, slot_word & fm]
+            e = x > full
+            differ = (x >> low) != (slot_word >> low)
+            assert np.all(~differ | ((x > slot_word) == e)), "a key prefix decided against the full key"
+            self.ties += int(np.sum(~differ))
+            return e
+
+        e0 = decide(w[:, 0], K[:, 0], fb)
+        i1 = 1 + e0.astype(np.int64)
+        e1 = decide(w[ar, i1], K[ar, i1], fb)
+        j = 2 * e0.astype(np.int64) + e1.astype(np.int64)
+        n2 = w[ar, 3 + j]
+        e2 = decide(n2, K[ar, 3 + j], fb + 2 * cb)
+        ex = 2 * j + e2.astype(np.int64)
+        mask = w[:, 7] >> 24
+        is_leaf = ((mask >> ex) & 1) == 1
+        nref = g_idx.astype(np.int64) + (w[:, 7] & 0xFFFFFF) + _popc8(~mask & ((1 << ex) - 1))
+        nref = np.where(is_leaf, LEAF, nref)
+        if g["n_values"]:
+            c3 = g["values3_base"] + 8 * g_idx.astype(np.int64) + ex
+        else:
+            c3 = (n2 >> (fb + cb * e2.astype(np.int64))) & ((1 << cb) - 1)
         return ex, nref, c3.astype(np.int32)

@@ -41,17 +41,19 @@ def _oracle(forest, X, leaves=False):
 
 
 def test_wide_forest_every_row(forests):
-    """64 trees, 50 classes, 100 features (its fields leave no room for
-    three-level super-nodes): all 100,000 test rows, in the library defaults
-    and in two other layouts."""
+    """64 trees, 50 classes, 100 features (its fields leave room for
+    three-level super-nodes of format 2 only): all 100,000 test rows, in the
+    library defaults and in three other layouts, one with two-level
+    super-nodes."""
     f = forests["wide"]
     X, _ = datagen.test_rows("wide")
     ref = _oracle(f, X, leaves=True)
     Xd = torch.from_numpy(X).cuda()
-    for params in ({}, dict(bin_size=16, interleave_depth=4, head_select=1), dict(bin_size=2, interleave_depth=7,
-                                                                                  pass_bytes=1 << 20)):
+    for params in ({}, dict(bin_size=16, interleave_depth=4, head_select=1),
+                   dict(bin_size=2, interleave_depth=7, pass_bytes=1 << 20),
+                   dict(bin_size=4, interleave_depth=5, deep_levels=2)):
         pk = fp.fp_pack_forest(f, **params)
-        assert pk.info()["deep_levels"] == 2
+        assert (pk.info()["deep_levels"], pk.info()["deep_format"]) == ((2, 0) if params.get("deep_levels") else (3, 2))
         df = fp.fp_upload(pk)
         votes, cls = df.predict(Xd)
         leaves = df.predict_leaves(Xd)
@@ -64,18 +66,19 @@ def test_wide_forest_every_row(forests):
 
 
 def test_batched_hbm_image_wide_one_launch_graph(forests):
-    """The HBM-resident forest (5 passes, three-level super-nodes, order-key
-    compares), the image forest (784 features, float compares), the wide
-    forest and a two-level packing of the HBM-resident forest in one
-    persistent launch, so both kinds of walk run in it; captured once,
+    """The HBM-resident forest (5 passes, three-level super-nodes of format
+    1), the image and wide forests (three-level super-nodes of format 2), a
+    two-level packing of the HBM-resident forest and the tiny forest in one
+    persistent launch, so every kind of walk runs in it; captured once,
     replayed on two sets of rows; every row compared with the oracle."""
     names = ["hbm", "image", "wide", "tiny", "hbm2"]
     sizes = [150_000, 20_011, 30_000, 4_099, 7_777]
     forests = dict(forests, hbm2=forests["hbm"])
     dfs = [fp.fp_upload(fp.fp_pack_forest(forests[k], deep_levels=2 if k == "hbm2" else 0)) for k in names]
     info = {k: d.info for k, d in zip(names, dfs)}
-    assert info["hbm"]["passes"] > 1 and info["hbm"]["deep_levels"] == 3
-    assert info["image"]["deep_levels"] == 2 and info["wide"]["deep_levels"] == 2
+    assert info["hbm"]["passes"] > 1 and (info["hbm"]["deep_levels"], info["hbm"]["deep_format"]) == (3, 1)
+    assert (info["image"]["deep_levels"], info["image"]["deep_format"]) == (3, 2)
+    assert (info["wide"]["deep_levels"], info["wide"]["deep_format"]) == (3, 2)
     assert info["hbm2"]["deep_levels"] == 2
     pools = {k: datagen.test_rows(k if k != "hbm2" else "hbm", 2 * n)[0] for k, n in zip(names, sizes)}
     Xs = [torch.empty((n, forests[k].n_features), dtype=torch.float32, device="cuda") for k, n in zip(names, sizes)]

@@ -15,6 +15,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+# (deep_levels, deep_format): two-level super-nodes, three-level of format 1
+# (full keys first) and of format 2 (remapped key prefixes in every slot)
+DEEP_KINDS = [(2, 0), (3, 1), (3, 2)]
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
     if not torch.cuda.is_available():
@@ -52,33 +57,34 @@ def _check_all(forest, X, ref=None, **params):
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 1, 3), (3, 3, 3), (1, 0, 1), (2, 3, 1), (1, 1, 2), (3, 3, 2),
                                      (3, 9, 0)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_hand_fixtures_on_gpu(name, B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_hand_fixtures_on_gpu(name, B, d, sel, dl, fmt):
     """±inf, NaN, -0.0, a subnormal and thresholds equal to inputs; ranked
     heads (sel 3), level heads (sel 1) and paired level heads (sel 2); super-
-    nodes of two and three levels."""
+    nodes of two and three levels (both formats)."""
     forest, X, exp = load(name)
     ref = dict(leaf=exp["leaf"], votes=exp["votes"], cls=exp["cls"])
-    _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    _check_all(forest, X, ref, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt)
 
 
 @pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (1, 0, 3), (5, 2, 3), (7, 6, 3), (4, 9, 3), (16, 4, 1), (1, 0, 1),
                                      (3, 8, 1), (1, 11, 1), (16, 5, 2), (4, 9, 2), (1, 11, 2), (2, 1, 2)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_tiny_workload(tiny_forest, tiny_rows, B, d, sel, dl, fmt):
     X, _ = tiny_rows
-    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt)
 
 
 @pytest.mark.parametrize("B,d,sel", [(4, 2, 1), (3, 1, 2), (2, 3, 3), (1, 0, 1)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_rows_on_thresholds(tiny_forest, tiny_rows, B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_rows_on_thresholds(tiny_forest, tiny_rows, B, d, sel, dl, fmt):
     """Observations on the forest's thresholds (exactly, or one float step
     off) and -0, infinities and NaN: with three-level super-nodes many
-    compares tie on the key prefix and are decided by the full keys."""
+    compares tie on the key prefix and are decided by the full keys (in
+    format 2 every row on a threshold ties)."""
     from edge_rows import rows_on_thresholds
     X = rows_on_thresholds(tiny_forest, tiny_rows[0], seed=12)
-    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    _check_all(tiny_forest, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt)
 
 
 @pytest.mark.parametrize("rows_kind", ["sampled", "on_thresholds"])
@@ -93,6 +99,7 @@ def test_short_key_prefixes(tiny_forest, tiny_rows, rows_kind):
     X[:, :16] = tiny_rows[0] if rows_kind == "sampled" else rows_on_thresholds(tiny_forest, tiny_rows[0], seed=15)
     for B, d, sel in [(4, 2, 1), (3, 1, 2), (2, 3, 3)]:
         _check_all(f, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=3)
+        _check_all(f, X, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=3, deep_format=2)
 
 
 @pytest.mark.parametrize("tile,warps", [(32, 1), (64, 3), (256, 8), (1024, 32)])
@@ -165,15 +172,18 @@ def test_plain_baseline_fixture(name):
     np.testing.assert_array_equal(c.cpu().numpy(), exp["cls"])
 
 
-@pytest.mark.parametrize("kinds", [(0, 0, 0, 0), (2, 2, 2, 2), (3, 2, 3, 2)])
+@pytest.mark.parametrize("kinds", [((0, 0),) * 4, ((2, 0),) * 4, ((3, 2),) * 4, ((3, 1), (2, 0), (3, 1), (2, 0)),
+                                   ((3, 2), (2, 0), (3, 1), (3, 2))])
 def test_batched_matches_single(tiny_forest, tiny_rows, kinds):
-    """One launch over four forests: all with three-level super-nodes (the
-    default here), all with two-level ones, or a mix of the two."""
+    """One launch over four forests: all with three-level super-nodes of
+    format 1 (the default here) or of format 2, all with two-level ones, or
+    mixes of the kinds."""
     X, _ = tiny_rows
     forests, Xs, refs = [], [], []
     for i, n in enumerate([1, 700, 33, 5000]):
+        dl, fmt = kinds[i]
         forests.append(fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=1 + 3 * i, interleave_depth=i,
-                                                      deep_levels=kinds[i])))
+                                                      deep_levels=dl, deep_format=fmt)))
         Xs.append(_dev(X[i * 10: i * 10 + n]))
         refs.append(oracle.predict(tiny_forest, X[i * 10: i * 10 + n]))
     votes = [torch.empty((x.shape[0], tiny_forest.n_classes), dtype=torch.int32, device="cuda") for x in Xs]
@@ -186,10 +196,14 @@ def test_batched_matches_single(tiny_forest, tiny_rows, kinds):
 
 
 def test_image_workload_10k():
-    """Image-shaped workload (784 features, 10 classes, 128 trees), 10,000 rows."""
+    """Image-shaped workload (784 features, 10 classes, 128 trees), 10,000
+    rows: the default (three-level super-nodes of format 2) and two-level
+    super-nodes."""
     forest = datagen.forest("image")
     X, _ = datagen.test_rows("image", 10000)
-    _check_all(forest, X)
+    ref = _check_all(forest, X)
+    assert fp.fp_pack_forest(forest).info()["deep_format"] == 2
+    _check_all(forest, X, ref, deep_levels=2)
 
 
 def test_image_workload_params_grid():

@@ -52,11 +52,11 @@ def _check(F, X, ref, exact=False, **params):
 
 
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 1, 1), (3, 3, 3), (1, 2, 1), (3, 9, 0)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_values_fixture_on_gpu(B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", [(2, 0), (3, 1), (3, 2)])
+def test_values_fixture_on_gpu(B, d, sel, dl, fmt):
     F, X, exp = load_values("values_small.txt")
     ref = oracle.predict_values(F, X)
-    _check(F, X, ref, exact=True, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    _check(F, X, ref, exact=True, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt)
 
 
 @pytest.mark.parametrize("params", [dict(bin_size=4, interleave_depth=9, head_select=1),
@@ -68,7 +68,10 @@ def test_values_fixture_on_gpu(B, d, sel, dl):
                                          obs_tile=128),
                                     dict(bin_size=4, interleave_depth=9, head_select=2, deep_levels=2),
                                     dict(bin_size=2, interleave_depth=4, head_select=1, pass_bytes=65536,
-                                         deep_levels=2)])
+                                         deep_levels=2),
+                                    dict(bin_size=4, interleave_depth=9, head_select=2, deep_format=2),
+                                    dict(bin_size=2, interleave_depth=4, head_select=1, pass_bytes=65536,
+                                         deep_format=2)])
 def test_regression_forest_layouts(small_regress, params):
     F, X, ref = small_regress
     if "pass_bytes" in params:

@@ -17,6 +17,11 @@ from packed_decode import Image, LEAF, thr_key
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+
+# (deep_levels, deep_format): two-level super-nodes, three-level of format 1
+# (full keys first) and of format 2 (remapped key prefixes in every slot)
+DEEP_KINDS = [(2, 0), (3, 1), (3, 2)]
+
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "forest_pack.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -41,22 +46,23 @@ def test_binding_has_no_cpu_path():
 @pytest.mark.parametrize("name", ["stump_split.txt", "chain_full.txt"])
 @pytest.mark.parametrize("B,d,sel", [(1, 0, 3), (2, 0, 3), (2, 1, 3), (3, 2, 3), (1, 5, 3), (1, 0, 1), (2, 1, 1),
                                      (3, 4, 1), (1, 1, 2), (2, 3, 2)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_packed_records_decode_to_fixture_leaves(name, B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_packed_records_decode_to_fixture_leaves(name, B, d, sel, dl, fmt):
     forest, X, exp = load(name)
-    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
+    pk = fp.fp_pack_forest(forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl, deep_format=fmt)
     leaf, cls = Image(pk.image()).walk(X)
     np.testing.assert_array_equal(leaf, exp["leaf"])
 
 
 @pytest.mark.parametrize("B,d,sel", [(16, 4, 3), (5, 0, 3), (1, 2, 3), (7, 7, 3), (16, 4, 1), (3, 0, 1), (1, 9, 1),
                                      (1, 11, 1), (3, 1, 2), (4, 9, 2), (1, 11, 2), (16, 5, 2)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_packed_records_decode_to_oracle_leaves(tiny_forest, tiny_rows, B, d, sel, dl, fmt):
     X, _ = tiny_rows
     ref = oracle.predict(tiny_forest, X[:3000])
-    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl)
-    assert pk.info()["deep_levels"] == dl
+    pk = fp.fp_pack_forest(tiny_forest, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl,
+                           deep_format=fmt)
+    assert pk.info()["deep_levels"] == dl and pk.info()["deep_format"] == fmt
     leaf, cls = Image(pk.image()).walk(X[:3000])
     np.testing.assert_array_equal(leaf, ref["leaf"])
     np.testing.assert_array_equal(cls, tiny_forest.leaf_class[tiny_forest.node_begin[:-1][None, :] + ref["leaf"]])
@@ -316,8 +322,8 @@ def test_null_arguments_rejected():
 
 
 @pytest.mark.parametrize("B,d,sel", [(4, 3, 1), (1, 0, 3), (3, 6, 3), (2, 9, 1), (3, 9, 0)])
-@pytest.mark.parametrize("dl", [2, 3])
-def test_value_forest_records_decode_to_oracle(B, d, sel, dl):
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
+def test_value_forest_records_decode_to_oracle(B, d, sel, dl, fmt):
     """A forest with leaf values: every leaf reference names a value slot
     holding the leaf's value, and the walk reaches the oracle's leaves."""
     import datagen
@@ -325,7 +331,8 @@ def test_value_forest_records_decode_to_oracle(B, d, sel, dl):
     F = datagen.train_regression(X, y, 6, mtry=9, min_leaf=3, seed=21, threads=4)
     Xt, _ = datagen.gen_regression(21, 1500, 1, 1.0, 1.0)
     ref = oracle.predict_values(F, Xt)
-    im = Image(fp.fp_pack_forest(F, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl).image())
+    im = Image(fp.fp_pack_forest(F, bin_size=B, interleave_depth=d, head_select=sel, deep_levels=dl,
+                                 deep_format=fmt).image())
     n_leaves = int((F.left < 0).sum())
     assert im.h["values3_base"] == n_leaves
     assert im.h["n_values"] == n_leaves + (8 * im.h["n_super"] if dl == 3 else 0)
@@ -334,20 +341,36 @@ def test_value_forest_records_decode_to_oracle(B, d, sel, dl):
     np.testing.assert_array_equal(im.values[slot], F.leaf_value[F.node_begin[:-1][None, :] + ref["leaf"]])
 
 
+def _kind(forest, **kw):
+    i = fp.fp_pack_forest(forest, **kw).info()
+    return i["deep_levels"], i["deep_format"]
+
+
 def test_deep_levels_follow_field_widths():
-    """Three-level super-nodes hold two features and two classes beside the
-    last level's key prefix: by default they are used when those fields take
-    at most 16 bits, on request up to 24, and refused beyond."""
+    """Three-level super-nodes of format 1 hold two features and two classes
+    beside the last level's key prefix: by default when those fields take at
+    most 16 bits, on request up to 24.  Format 2 holds one feature per slot
+    (and the classes in the last level): by default when fb + 2 cb <= 20, on
+    request up to 24.  Beyond both, two-level super-nodes."""
     forest, _, _ = load("stump_split.txt")
-    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 3
-    forest.n_features, forest.n_classes = 784, 10  # 2 * 10 + 2 * 4 = 28 bits
-    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 2
+    assert _kind(forest) == (3, 1)
+    assert _kind(forest, deep_format=2) == (3, 2)
+    assert _kind(forest, deep_levels=2) == (2, 0)
+    forest.n_features, forest.n_classes = 784, 10  # format 1: 28 bits; format 2: 10 + 8
+    assert _kind(forest) == (3, 2)
+    assert _kind(forest, deep_levels=3) == (3, 2)
+    assert _kind(forest, deep_format=1) == (2, 0)  # format 1 asked for by default: does not fit
+    with pytest.raises(fp.FPError) as ei:
+        fp.fp_pack_forest(forest, deep_levels=3, deep_format=1)
+    assert ei.value.code == fp.FP_EUNSUPPORTED
+    forest.n_features, forest.n_classes = 100, 30  # format 1: 24 bits, on request; format 2: 7 + 10
+    assert _kind(forest) == (3, 2)
+    assert _kind(forest, deep_levels=3) == (3, 1)
+    forest.n_features, forest.n_classes = 1000, 200  # format 2: 10 + 16 bits
+    assert _kind(forest) == (2, 0)
     with pytest.raises(fp.FPError) as ei:
         fp.fp_pack_forest(forest, deep_levels=3)
     assert ei.value.code == fp.FP_EUNSUPPORTED
-    forest.n_features, forest.n_classes = 100, 30  # 2 * 7 + 2 * 5 = 24 bits: on request only
-    assert fp.fp_pack_forest(forest).info()["deep_levels"] == 2
-    assert fp.fp_pack_forest(forest, deep_levels=3).info()["deep_levels"] == 3
 
 
 def test_value_forest_rejects_non_finite_values():
@@ -361,9 +384,9 @@ def test_value_forest_rejects_non_finite_values():
     assert ei.value.code == fp.FP_EINVAL
 
 
-@pytest.mark.parametrize("dl", [2, 3])
+@pytest.mark.parametrize("dl,fmt", DEEP_KINDS)
 @pytest.mark.parametrize("sel", [1, 3])
-def test_rows_on_thresholds_decode_to_oracle_leaves(tiny_forest, tiny_rows, dl, sel):
+def test_rows_on_thresholds_decode_to_oracle_leaves(tiny_forest, tiny_rows, dl, fmt, sel):
     """Observations equal to the forest's thresholds (or one float step off),
     and -0, infinities and NaN: the key compares give the oracle's leaves,
     and with three-level super-nodes the key-prefix ties are decided by the
@@ -372,7 +395,7 @@ def test_rows_on_thresholds_decode_to_oracle_leaves(tiny_forest, tiny_rows, dl, 
     X = rows_on_thresholds(tiny_forest, tiny_rows[0][:3000], seed=11)
     ref = oracle.predict(tiny_forest, X)
     im = Image(fp.fp_pack_forest(tiny_forest, bin_size=4, interleave_depth=2, head_select=sel,
-                                 deep_levels=dl).image())
+                                 deep_levels=dl, deep_format=fmt).image())
     leaf, cls = im.walk(X)
     np.testing.assert_array_equal(leaf, ref["leaf"])
     if dl == 3:
@@ -488,3 +511,93 @@ def test_short_key_prefixes_decode_to_oracle_leaves(tiny_forest, tiny_rows):
     leaf, _ = im.walk(X)
     np.testing.assert_array_equal(leaf, ref["leaf"])
     assert im.ties > 300
+
+
+def _remap_of(im):
+    return lambda k: int(im.remap(np.array([k], np.int64))[0])
+
+
+@pytest.mark.parametrize("thresholds", [
+    [0.25, 0.5, 0.75, 1e-20, 0.9999999],                  # one sign
+    [-3.0, 2.5, 0.0, 1e-3, -1e-30],                       # both signs, a narrow range
+    [-2.0, -1e-3, 1e-3, 2.0, 0.5, -0.5],                  # both signs: the run around zero collapsed
+    [-1e30, 1e30, 0.0],
+    [-3e38, -1e10, -1.0, -1e-10, 1e-10, 1.0, 1e10, 3e38],  # spread over the whole key range
+    [np.inf, -np.inf, 1.0],                                # infinite thresholds
+    [1.5],                                                 # one threshold, no run to collapse
+    [1.0, np.nextafter(np.float32(1.0), np.float32(2.0))],  # adjacent keys
+])
+def test_key_remap_is_exact(thresholds):
+    """Format 2 compares V(key(x)) with V(key(t)): for every value x (signed
+    zeros, subnormals, infinities, NaN, values below, inside and above the
+    thresholds' range, inside the collapsed run, each threshold's float
+    neighbours) and every threshold t of the forest, V(key(x)) <= V(key(t))
+    exactly when x <= t; every row value lies above the stored word of a NaN
+    threshold or a dummy slot (0); the run collapsed is the widest one
+    between adjacent threshold keys, and the shift is dropped exactly when
+    the remaining range needs 32 bits."""
+    from packed_decode import obs_key
+    th = np.array(thresholds, np.float32)
+    n = th.size
+    # a chain: internal node i has leaf n + i on its left and node i + 1 (the
+    # last one: leaf 2n) on its right
+    left = np.array([n + i for i in range(n)] + [-1] * (n + 1), np.int32)
+    right = np.array([i + 1 for i in range(n - 1)] + [2 * n] + [-1] * (n + 1), np.int32)
+    f = datagen.Forest(2, 2, np.array([0, 2 * n + 1], np.int64), left, right, np.zeros(2 * n + 1, np.int32),
+                       np.concatenate([th, np.zeros(n + 1, np.float32)]), np.zeros(2 * n + 1, np.int32),
+                       np.zeros(2 * n + 1, np.int64))
+    im = Image(fp.fp_pack_forest(f, deep_levels=3, deep_format=2, interleave_depth=0).image())
+    assert im.fmt == 2
+    keys = np.unique(thr_key(th).astype(np.int64))
+    widest = int(np.diff(keys).max()) if keys.size > 1 else 0
+    span = int(keys.max()) + 1 - int(keys.min()) - max(0, widest - 2)
+    assert (im.h["key_flag"] == 0) == (span >= 1 << 31)
+    assert im.h["key_gap_d"] == max(0, widest - 2)
+    probes = [0.0, -0.0, 1e-45, -1e-45, 1e-38, -1e-38, 1.0, -1.0, 3.4e38, -3.4e38, np.inf, -np.inf, 0.5, 2.0,
+              -5.0, 7e-21, 1e-4, -1e-4, 1e-2, -1e-2, 1e20, -1e20]
+    for t in th:
+        for step in (np.float32(np.inf), np.float32(-np.inf)):
+            probes.append(np.nextafter(t, step))
+        probes.append(t)
+    x = np.array(probes, np.float32)
+    vx = im.remap(obs_key(x).astype(np.int64))
+    vt = im.word(th).astype(np.int64)
+    for i in range(x.size):
+        for j in range(th.size):
+            assert (vx[i] <= vt[j]) == bool(x[i] <= th[j]), (x[i], th[j])
+    nan = np.array([np.nan], np.float32)
+    assert im.remap(obs_key(nan).astype(np.int64))[0] > vt.max()
+    assert int(im.word(nan)[0]) == 0
+    if im.h["key_flag"]:
+        assert np.all(vx >= 0x80000000)  # never equal in the top bit to a dummy's 0
+
+
+def test_three_level_format2_super_nodes(tiny_forest):
+    """Format 2 (fp_internal.h): every slot word is the top bits of the
+    slot's remapped key over its feature (32 - fb prefix bits in slots 0..2,
+    32 - fb - 2 cb in slots 3..6, whose words also hold their exits' classes);
+    the side table holds the seven full remapped keys and a zero; dummies are
+    0; leaf mask, offsets and leaf ids as in format 1."""
+    f = tiny_forest
+    pk = fp.fp_pack_forest(f, bin_size=4, interleave_depth=1, head_select=1, deep_levels=3, deep_format=2)
+    im = Image(pk.image())
+    fb, cb = im.h["feature_bits"], im.h["class_bits"]
+    assert (fb, cb) == (4, 2) and im.fmt == 2 and im.h["key_flag"] == 0x80000000
+    fm = (1 << fb) - 1
+    n_checked = 0
+    for g in range(im.h["n_super"]):
+        w = [int(x) for x in im.sw[g]]
+        K = [int(x) for x in im.deep_keys[g]]
+        assert K[7] == 0
+        for i in range(7):
+            low = fb if i < 3 else fb + 2 * cb
+            assert w[i] >> low == K[i] >> low
+            if K[i] == 0:  # a dummy slot: nothing but (possibly) exit classes
+                assert w[i] & fm == 0 and w[i] >> low == 0
+            else:
+                assert K[i] >= 0x80000000
+                n_checked += 1
+    assert n_checked > 100
+    # every stored full key is a remapped threshold of the forest
+    allk = set(int(v) for v in im.word(f.threshold[f.left >= 0]))
+    assert set(int(k) for k in im.deep_keys[:, :7].reshape(-1) if k) <= allk
