@@ -22,9 +22,13 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("name,n,world,bin_size", [("tiny", 10000, 2, 2), ("tiny", 10000, 3, 1),
-                                                   ("wide", 20000, 3, 4), ("hbm", 30000, 4, 4)])
-def test_shards_sum_to_the_whole_forest(name, n, world, bin_size):
+@pytest.mark.parametrize("name,n,world,bin_size,fmt", [("tiny", 10000, 2, 2, 0), ("tiny", 10000, 3, 1, 0),
+                                                       ("wide", 20000, 3, 4, 0), ("hbm", 30000, 4, 4, 0),
+                                                       ("tiny", 10000, 3, 2, 2), ("hbm", 30000, 3, 4, 2)])
+def test_shards_sum_to_the_whole_forest(name, n, world, bin_size, fmt):
+    """fmt 2: three-level super-nodes of format 2 forced, so every shard
+    remaps its keys onto its own trees' thresholds (the wide forest takes
+    format 2 by default)."""
     forest = datagen.forest(name)
     X, _ = datagen.test_rows(name, n)
     Xd = torch.from_numpy(X).cuda()
@@ -34,7 +38,7 @@ def test_shards_sum_to_the_whole_forest(name, n, world, bin_size):
         b, e = fp.fp_shard_trees(forest, bin_size, world, k)
         if e == b:
             continue
-        df = fp.fp_upload(fp.fp_pack_forest_trees(forest, b, e, bin_size=bin_size))
+        df = fp.fp_upload(fp.fp_pack_forest_trees(forest, b, e, bin_size=bin_size, deep_format=fmt))
         votes = torch.empty((n, forest.n_classes), dtype=torch.int32, device="cuda")
         fp.fp_predict(df, Xd, votes, None)
         total += votes

@@ -39,13 +39,16 @@ def _call(df, X, votes, cls):
 
 
 @pytest.mark.parametrize("pass_bytes", [2048, -1])
-def test_noalloc_matches_fp_predict_twice(pass_bytes):
+@pytest.mark.parametrize("deep_format", [1, 2])
+def test_noalloc_matches_fp_predict_twice(pass_bytes, deep_format):
     """Two calls in a row give exactly fp_predict's votes and classes, and
     the oracle's, with scratch in use (several passes) and without (one
-    pass)."""
+    pass), for three-level super-nodes of either format."""
     X, y = datagen.rows("tiny", 0)
     forest = datagen.train_forest(X, y, 4, 16, 4, seed=0)
-    pk = fp.fp_pack_forest(forest, bin_size=2, interleave_depth=2, pass_bytes=pass_bytes, obs_tile=128)
+    pk = fp.fp_pack_forest(forest, bin_size=2, interleave_depth=2, pass_bytes=pass_bytes, obs_tile=128,
+                           deep_format=deep_format)
+    assert pk.info()["deep_format"] == deep_format
     assert (pk.info()["passes"] > 1) == (pass_bytes > 0)
     df = fp.fp_upload(pk)
     Xt, _ = datagen.test_rows("tiny", 3001)
