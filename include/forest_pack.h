@@ -260,11 +260,16 @@ int fp_predict_values(const fp_device_forest *forest, const float *X, int64_t n,
                       float *out, void *stream);
 
 /* fp_predict and fp_predict_values for rows and results in host memory: the
- * rows go to the device in chunks of chunk_rows (0: a quarter of n, at least
+ * rows go to the device in chunks of chunk_rows (0: an eighth of n, at least
  * 65,536) through two device buffers; chunk c+1 is copied in on a copy
- * stream the library keeps per device while chunk c is classified on
- * `stream`, and each chunk's outputs are copied back on `stream` after its
- * kernel.  Device memory for the buffers comes from the stream-ordered pool.
+ * stream the library keeps per device while chunk c is classified.  The
+ * chunks of the first buffer are classified on `stream`, those of the second
+ * on a second stream the library keeps per device (so a chunk's kernel
+ * starts on the SMs the previous one has left); each chunk's outputs are
+ * copied back on its kernel's stream, and `stream` waits for the second
+ * stream before the call's last work, so completion of `stream` covers
+ * everything.  Device memory for the buffers comes from the stream-ordered
+ * pool.
  *   X_host          host, [n][n_features] FP32 row-major; page-locked memory
  *                   (cudaHostAlloc, or a pinned torch tensor) lets the copies
  *                   overlap the kernels, ordinary memory works but copies

@@ -739,70 +739,89 @@ extern "C" int fp_predict_batched(const fp_device_forest *const *forests, const 
 namespace {
 
 std::mutex g_copy_mu;
-std::vector<cudaStream_t> g_copy_stream;  // per device, created on first use, kept for the process
+// per device, created on first use, kept for the process: [0] the copy
+// stream, [1] a second stream for every other chunk's kernel
+std::vector<cudaStream_t> g_lib_stream[2];
 
-int copy_stream(int device, cudaStream_t *out) {
+int lib_stream(int device, int which, cudaStream_t *out) {
     std::lock_guard<std::mutex> lk(g_copy_mu);
-    if ((int)g_copy_stream.size() <= device) g_copy_stream.resize((size_t)device + 1, nullptr);
-    if (!g_copy_stream[device]) {
-        cudaError_t e = cudaStreamCreateWithFlags(&g_copy_stream[device], cudaStreamNonBlocking);
+    std::vector<cudaStream_t> &v = g_lib_stream[which];
+    if ((int)v.size() <= device) v.resize((size_t)device + 1, nullptr);
+    if (!v[device]) {
+        cudaError_t e = cudaStreamCreateWithFlags(&v[device], cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-            g_copy_stream[device] = nullptr;
-            return cuda_fail(e, "cudaStreamCreateWithFlags(copy)");
+            v[device] = nullptr;
+            return cuda_fail(e, which ? "cudaStreamCreateWithFlags(compute)" : "cudaStreamCreateWithFlags(copy)");
         }
     }
-    *out = g_copy_stream[device];
+    *out = v[device];
     return FP_OK;
 }
 
-// Rows from host memory through the device in chunks: chunk c's rows are
-// copied in on the library's copy stream while chunk c-1 is classified on
-// the caller's stream, into one of two device buffers; each chunk's outputs
-// are copied back on the caller's stream after its kernel.  out_bytes: bytes
-// of output per row (one region per output); run(Xd, rows, outs) launches
-// the chunk's classification on `s`.
+// Rows from host memory through the device in chunks (eight by default):
+// chunk c's rows are copied in on the library's copy stream into one of two
+// device buffers while earlier chunks are classified; the chunks of buffer 0
+// are classified on the caller's stream and those of buffer 1 on a second
+// library stream, so that a chunk's kernel starts on the SMs that the
+// previous chunk's kernel has left, instead of after its last CTA; each
+// chunk's outputs are copied back on its kernel's stream.  The caller's
+// stream waits for the second one before the buffers are released, so all
+// the work is ordered before whatever the caller enqueues next.  out_bytes:
+// bytes of output per row (one region per output); run(Xd, rows, outs,
+// stream) launches the chunk's classification on `stream`.
 template <class Run>
 int pipeline_host(const fp_device_forest *f, const float *X_host, int64_t n, int64_t chunk_rows,
                   const int64_t out_bytes[2], void *const out_host[2], cudaStream_t s, const char *what, Run run) {
     const int64_t F = f->hdr.n_features;
-    const int64_t chunk = std::min<int64_t>(n, chunk_rows > 0 ? chunk_rows : std::max<int64_t>(65536, (n + 3) / 4));
+    const int64_t chunk = std::min<int64_t>(n, chunk_rows > 0 ? chunk_rows : std::max<int64_t>(65536, (n + 7) / 8));
     const int nbuf = n > chunk ? 2 : 1;
     auto align = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
     const int64_t in_b = align(chunk * F * 4), o0 = align(chunk * out_bytes[0]), o1 = align(chunk * out_bytes[1]);
     const int64_t per_buf = in_b + o0 + o1;
-    cudaStream_t cs = nullptr;
-    int rc = copy_stream(f->device, &cs);
+    cudaStream_t cs = nullptr, s2 = nullptr;
+    int rc = lib_stream(f->device, 0, &cs);
+    if (rc == FP_OK && nbuf == 2) rc = lib_stream(f->device, 1, &s2);
     if (rc) return rc;
     void *block = nullptr;
     rc = scratch_alloc(f->device, &block, (size_t)(nbuf * per_buf), s);
     if (rc) return rc;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // ready, in[2], free[2]
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // ready, in[2], free[2], s2 done
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);  // the block is allocated
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);  // the block is allocated; earlier work on s is ordered
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+    if (e == cudaSuccess && s2) e = cudaStreamWaitEvent(s2, ev[0], 0);
+    bool s2_used = false;
     uint8_t *base = static_cast<uint8_t *>(block);
     for (int64_t c = 0, r0 = 0; e == cudaSuccess && rc == FP_OK && r0 < n; ++c, r0 += chunk) {
         const int b = (int)(c % nbuf);
+        cudaStream_t ks = b == 0 ? s : s2;  // the chunk's kernel and output copies
+        s2_used |= b == 1;
         const int64_t rows = std::min<int64_t>(chunk, n - r0);
         uint8_t *buf = base + b * per_buf;
         if (c >= nbuf) e = cudaStreamWaitEvent(cs, ev[3 + b], 0);  // chunk c-2 is done with the buffer
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(buf, X_host + r0 * F, (size_t)(rows * F * 4), cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1 + b], cs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, ev[1 + b], 0);
         if (e != cudaSuccess) break;
         void *outs[2] = {out_host[0] ? buf + in_b : nullptr, out_host[1] ? buf + in_b + o0 : nullptr};
-        rc = run(reinterpret_cast<const float *>(buf), rows, outs);
+        rc = run(reinterpret_cast<const float *>(buf), rows, outs, ks);
         for (int k = 0; k < 2 && rc == FP_OK && e == cudaSuccess; ++k)
             if (out_host[k])
                 e = cudaMemcpyAsync(static_cast<uint8_t *>(out_host[k]) + r0 * out_bytes[k], outs[k],
-                                    (size_t)(rows * out_bytes[k]), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + b], s);
+                                    (size_t)(rows * out_bytes[k]), cudaMemcpyDeviceToHost, ks);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + b], ks);
+    }
+    if (s2_used) {  // the caller's stream covers the second stream's work, errors or not
+        cudaError_t e2 = cudaEventRecord(ev[5], s2);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev[5], 0);
+        if (e2 != cudaSuccess) cudaStreamSynchronize(s2);
+        if (e == cudaSuccess) e = e2;
     }
     if (e != cudaSuccess || rc != FP_OK) cudaStreamSynchronize(cs);  // nothing of the copy stream outlives the block
     cudaFreeAsync(block, s);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
     if (e != cudaSuccess) return cuda_fail(e, what);
     return rc;
@@ -827,9 +846,9 @@ extern "C" int fp_predict_host(const fp_device_forest *f, const float *X_host, i
     const int64_t ob[2] = {4 * (int64_t)f->hdr.n_classes, 4};
     void *const oh[2] = {out_votes_host, out_class_host};
     return pipeline_host(f, X_host, n, chunk_rows, ob, oh, s, "fp_predict_host",
-                         [&](const float *Xd, int64_t rows, void *const outs[2]) {
+                         [&](const float *Xd, int64_t rows, void *const outs[2], cudaStream_t ks) {
                              return fp_predict(f, Xd, rows, static_cast<uint32_t *>(outs[0]),
-                                               static_cast<int32_t *>(outs[1]), s);
+                                               static_cast<int32_t *>(outs[1]), ks);
                          });
 }
 
@@ -850,8 +869,8 @@ extern "C" int fp_predict_values_host(const fp_device_forest *f, const float *X_
     const int64_t ob[2] = {4, 0};
     void *const oh[2] = {out_host, nullptr};
     return pipeline_host(f, X_host, n, chunk_rows, ob, oh, s, "fp_predict_values_host",
-                         [&](const float *Xd, int64_t rows, void *const outs[2]) {
-                             return fp_predict_values(f, Xd, rows, scale, bias, static_cast<float *>(outs[0]), s);
+                         [&](const float *Xd, int64_t rows, void *const outs[2], cudaStream_t ks) {
+                             return fp_predict_values(f, Xd, rows, scale, bias, static_cast<float *>(outs[0]), ks);
                          });
 }
 

@@ -1,9 +1,10 @@
 """GPU parity for the host-buffer entry points (fp_predict_host,
 fp_predict_values_host): rows in host memory go through the device in
-chunks, copies on a copy stream overlapping the kernels on the caller's
-stream.  Classes, votes and leaf-value outputs must equal the oracle's (bit
-for bit; values within the float32 bound) for every chunking, including
-ragged last chunks, single rows and pageable inputs."""
+chunks, copies on a copy stream overlapping the kernels, which alternate
+between the caller's stream and a second library stream.  Classes, votes
+and leaf-value outputs must equal the oracle's (bit for bit; values within
+the float32 bound) for every chunking, including ragged last chunks, single
+rows and pageable inputs, once the caller's stream alone is synchronised."""
 import numpy as np
 import pytest
 
@@ -46,6 +47,25 @@ def test_host_classes_and_votes(tiny_forest, tiny_rows, tiny_df, n, chunk):
     np.testing.assert_array_equal(votes.numpy().astype(np.uint32), ref["votes"])
 
 
+@pytest.mark.parametrize("chunk", [0, 613])
+def test_host_on_a_nonblocking_stream(tiny_forest, tiny_rows, tiny_df, chunk):
+    """On a stream of the caller's own that does not synchronise with the
+    legacy default stream: waiting for that stream alone covers every
+    chunk's kernel and copies, those on the library's second stream too;
+    then the same buffers are reused at once."""
+    X = np.ascontiguousarray(tiny_rows[0][:9000])
+    ref = oracle.predict(tiny_forest, X)
+    Xp = torch.from_numpy(X).pin_memory()
+    s = torch.cuda.Stream()
+    for rep in range(2):
+        votes = torch.full((9000, tiny_forest.n_classes), -1, dtype=torch.int32).pin_memory()
+        cls = torch.full((9000,), -1, dtype=torch.int32).pin_memory()
+        fp.fp_predict_host(tiny_df, Xp, votes, cls, chunk, s)
+        s.synchronize()
+        np.testing.assert_array_equal(cls.numpy(), ref["cls"])
+        np.testing.assert_array_equal(votes.numpy().astype(np.uint32), ref["votes"])
+
+
 def test_host_pageable_numpy_and_method(tiny_forest, tiny_rows, tiny_df):
     X = np.ascontiguousarray(tiny_rows[0][:5000])
     ref = oracle.predict(tiny_forest, X)
@@ -70,8 +90,9 @@ def test_host_three_and_two_level_super_nodes(tiny_forest, tiny_rows):
 
 
 def test_host_hbm_rows_match_device_path():
-    """500,000 rows of the HBM-resident workload: the host path in 4 chunks
-    gives the classes of the device path; a sample equals the oracle."""
+    """500,000 rows of the HBM-resident workload: the host path in 8 chunks
+    (two compute streams, five passes each) gives the classes of the device
+    path; a sample equals the oracle."""
     forest = datagen.forest("hbm")
     X, _ = datagen.test_rows("hbm", 500000)
     df = fp.fp_upload(fp.fp_pack_forest(forest))
