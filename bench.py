@@ -868,8 +868,10 @@ def run_ablation(args, ws, rank, local):
     no_stats = datagen.Forest(forest.n_features, forest.n_classes, forest.node_begin, forest.left, forest.right,
                               forest.feature, forest.threshold, forest.leaf_class, forest.cardinality)
     no_stats.cardinality = None  # packed without statistics: children keep left-first order
-    best = at.autotune(forest, X[: min(n, 1 << 20)], layouts=HBM_LAYOUTS if name == "hbm" else None,
-                       launches=HBM_LAUNCHES if name == "hbm" else None)
+    layouts, launches = TUNE.get(name, (None, None))
+    best = at.autotune(forest, X[: min(n, 1 << 20)], layouts=layouts, launches=launches)
+    tuned_layout = {k: best[k] for k in at.LAYOUT_KEYS}
+    two_level = dict(tuned_layout, deep_levels=2, deep_format=0)
     # the paper's layouts with two-level super-nodes (full thresholds), then
     # the same with three-level ones, then the autotuner's choice
     variants = [
@@ -887,7 +889,9 @@ def run_ablation(args, ws, rank, local):
          {}),
         ("Bin B=3, levels 0..8, three-level super-nodes", forest,
          dict(bin_size=3, interleave_depth=8, head_select=1, deep_levels=3), {}),
-        ("autotuned", forest, {k: best[k] for k in at.LAYOUT_KEYS}, {k: best[k] for k in at.LAUNCH_KEYS}),
+        ("autotuned layout and launch, two-level super-nodes", forest, two_level,
+         {k: best[k] for k in at.LAUNCH_KEYS}),
+        ("autotuned", forest, tuned_layout, {k: best[k] for k in at.LAUNCH_KEYS}),
     ]
     for label, f, params, launch in variants:
         df = fp.fp_upload(fp.fp_pack_forest(f, **params))
