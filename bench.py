@@ -268,6 +268,60 @@ def dist_setup(args):
     return ws, rank, local
 
 
+class L2Flush:
+    """For a workload whose inputs fit in L2: a write of twice the L2 size
+    before every timed step evicts them, so each step starts from a cold L2
+    as a step of a larger workload would."""
+
+    def __init__(self, dev):
+        import torch
+        self.l2 = int(torch.cuda.get_device_properties(dev).L2_cache_size)
+        self.buf = torch.empty((2 * self.l2) // 4, dtype=torch.int32, device=dev)
+
+    def __call__(self, stream) -> None:
+        import torch
+        with torch.cuda.stream(stream):
+            self.buf.fill_(1)
+
+    def describe(self, input_bytes: int) -> str:
+        return (f"inputs ({input_bytes / 1e6:.1f} MB) fit in L2 ({self.l2 / 1e6:.0f} MB): L2 flushed before every "
+                f"timed step by a {2 * self.l2 / 1e6:.0f} MB write, outside the step's events")
+
+
+def flush_for(dev, input_bytes: int):
+    """An L2Flush when the workload's inputs fit in L2, else None."""
+    import torch
+    l2 = int(torch.cuda.get_device_properties(dev).L2_cache_size)
+    return L2Flush(dev) if input_bytes < l2 else None
+
+
+def timed_steps(fn, k: int, stream, flush=None):
+    """Device milliseconds of k steps of fn() on `stream`, and the per-step
+    times when measured: one event pair around k back-to-back steps (inputs
+    larger than L2), or with an L2 flush before every step one event pair per
+    step (the flush outside it), summed."""
+    import torch
+    if flush is None:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), None
+    ev = []
+    for _ in range(k):
+        flush(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    return sum(per), per
+
+
 def max_over_ranks(value: float, ws: int, device=None) -> float:
     """The largest value over all ranks (the slowest rank's time); the value
     itself with one rank."""
@@ -396,31 +450,29 @@ def run_packed(args, ws, rank, local):
     if status != fp.FP_OK:
         raise RuntimeError(f"kernel status {status}: {fp.fp_last_error()}")
 
+    flush = flush_for(dev, Xh.nbytes + info["total_bytes"])
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
     # the timed region: K steps, one launch each, back to back on the stream
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for i in range(args.steps):
-        step(X, votes, cls, stream)
-    stop.record(stream)
-    torch.cuda.synchronize()
+    # (inputs larger than L2), or each after an L2 flush and timed alone
+    total_ms, per_launch_ms = timed_steps(lambda: step(X, votes, cls, stream), args.steps, stream, flush)
     barrier()
     clk = clocks.stop()
-    total_ms = start.elapsed_time(stop)
-    # the spread of single launches, in a separate pass with events around
-    # each (recording them costs host time between launches, so they stay out
-    # of the timed region)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        step(X, votes, cls, stream)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if per_launch_ms is None:
+        # the spread of single launches, in a separate pass with events around
+        # each (recording them costs host time between launches, so they stay
+        # out of the timed region)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step(X, votes, cls, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        per_launch_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(total_ms, ws, dev)
     value = ws * n * args.steps / (total_ms / 1e3)
 
@@ -442,13 +494,7 @@ def run_packed(args, ws, rank, local):
             plain_step(order)
             torch.cuda.synchronize()
             ks = max(2, args.steps // 4)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(ks):
-                plain_step(order)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / ks
+            ms = timed_steps(lambda: plain_step(order), ks, stream, flush)[0] / ks  # as the packed path
             cand = {"order": oname, "value": n / (ms / 1e3), "ms_per_step": ms}
             if values:
                 cand["max_abs_diff"] = float((pc - cls).abs().max())
@@ -556,8 +602,9 @@ def run_packed(args, ws, rank, local):
                     {"workload": name, "desc": WORKLOADS[name]["desc"], "rows": n, "n_trees": T, "n_features": F,
                      "n_classes": C, **params, "passes": info["passes"], "forest_bytes": info["total_bytes"],
                      "autotuned": tuning is not None, "parallelism": f"replicas x{ws}",
-                     "l2": "inputs larger than L2 (rows %.0f MB, forest %.0f MB); no flush" %
-                           (Xh.nbytes / 1e6, info["total_bytes"] / 1e6)})
+                     "l2": flush.describe(Xh.nbytes + info["total_bytes"]) if flush else
+                     "inputs larger than L2 (rows %.0f MB, forest %.0f MB); no flush" %
+                     (Xh.nbytes / 1e6, info["total_bytes"] / 1e6)})
     out.update({
         "plain_baseline": plain,
         "packed_vs_plain": (value / ws / plain["value"]) if plain else None,
@@ -612,17 +659,14 @@ def run_batched(args, ws, rank, local):
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
+    input_bytes = sum(x.nbytes for x in Xh) + sum(d.info["total_bytes"] for d in dfs)
+    flush = flush_for(dev, input_bytes)
+    cur = torch.cuda.current_stream()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        g.replay()
-    b.record()
-    torch.cuda.synchronize()
+    total_ms, _ = timed_steps(g.replay, args.steps, cur, flush)
     clk = clocks.stop()
-    total_ms = a.elapsed_time(b)
     rows = sum(sizes)
     value = ws * rows * args.steps / (total_ms / 1e3)
     for d in dfs:
@@ -687,14 +731,15 @@ def run_batched(args, ws, rank, local):
                 "bytes_kind": "algorithmic: 8 B per internal node visited (oracle count) + rows + votes + classes",
                 "node_visits_per_s": visits / launch_s,
                 "hbm": {"peak": peak_hbm, "peak_kind": peak_kind, "algorithmic_frac": achieved / peak_hbm,
-                        "note": "forests and rows stay L2-resident across replays; not a DRAM fraction"}}
+                        "note": "the forests' nodes come from shared memory and L2; not a DRAM fraction"}}
     check_roofline(roofline)
     out = base_line(args, ws, value, total_ms,
                     {"workload": "batched", "desc": WORKLOADS["batched"]["desc"], "batch_rows": sizes,
                      "n_trees": [f.n_trees for f in forests], "parallelism": f"replicas x{ws}",
                      "layout": {k: tuning.get(k) for k in ("bin_size", "interleave_depth", "head_select",
                                                            "deep_levels", "deep_format", "launch")},
-                     "l2": "forests and rows L2-resident across replays (graph replay of the same inputs)"})
+                     "l2": flush.describe(input_bytes) if flush else
+                     "inputs larger than L2 (%.0f MB); no flush" % (input_bytes / 1e6)})
     out.update({"gpu_launches": args.steps, "graph": "one persistent launch per replay", "clocks": clk,
                 "e2e": e2e, "roofline": roofline,
                 "parity_checked": {"rows": rows, "mismatches": 0, "compared": "votes and class of every row"},
