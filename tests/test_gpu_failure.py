@@ -60,8 +60,13 @@ def test_injected_scratch_allocation_failure(tiny_forest, tiny_rows):
 
 
 @pytest.mark.parametrize("params", [dict(bin_size=4, interleave_depth=3),
-                                    dict(bin_size=2, interleave_depth=2, pass_bytes=2048)])
+                                    dict(bin_size=2, interleave_depth=2, pass_bytes=2048),
+                                    dict(bin_size=4, interleave_depth=3, deep_format=2),
+                                    dict(bin_size=4, interleave_depth=3, deep_levels=2)])
 def test_stalled_bin_copy_times_out_and_recovers(tiny_forest, tiny_rows, params):
+    """Every kind of super-node has its own compiled walk, each with the
+    bounded bin wait: three-level of format 1 (the default here), of format
+    2, and two-level."""
     Xh, Xd = _rows(tiny_rows, 5000)
     df = fp.fp_upload(fp.fp_pack_forest(tiny_forest, **params))
     fp.fp_inject_fault(df, fp.FP_FAULT_WAIT_LIMIT, 4096)
@@ -80,16 +85,18 @@ def test_stalled_bin_copy_times_out_and_recovers(tiny_forest, tiny_rows, params)
     df.release()
 
 
-def test_stalled_forest_in_a_batched_launch(tiny_forest, tiny_rows):
+@pytest.mark.parametrize("fmt_good,fmt_bad", [(0, 0), (1, 2)])
+def test_stalled_forest_in_a_batched_launch(tiny_forest, tiny_rows, fmt_good, fmt_bad):
     """A stalled forest after a healthy one in one launch: the stalled
     forest's status records the timeout.  Work items are handed out batch by
     batch, so every item of the healthy forest was claimed before the first
     stalled item aborted a CTA; the healthy forest's status stays clean.  (A
     CTA that aborted records the timeout in the status of every later item it
-    skips, whichever forest the item belongs to.)"""
+    skips, whichever forest the item belongs to.)  With formats 1 and 2 the
+    launch compiles in both walks."""
     Xh, Xd = _rows(tiny_rows, 2000)
-    good = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=8, interleave_depth=2))
-    bad = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=8, interleave_depth=2))
+    good = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=8, interleave_depth=2, deep_format=fmt_good))
+    bad = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=8, interleave_depth=2, deep_format=fmt_bad))
     fp.fp_inject_fault(bad, fp.FP_FAULT_WAIT_LIMIT, 4096)
     fp.fp_inject_fault(bad, fp.FP_FAULT_STALL_BIN_COPY, 1)
     cls = [torch.empty((2000,), dtype=torch.int32, device="cuda") for _ in range(2)]
