@@ -93,15 +93,21 @@ typedef struct fp_forest_desc {
 } fp_forest_desc;
 
 /* Layout and launch parameters; 0 selects the default (for interleave_depth,
- * -1 does, since 0 is a valid depth).
+ * -1 does, since 0 is a valid depth).  The defaults depend on the row width:
+ * for rows of more than 384 features ("wide rows") they are bins of 32 trees,
+ * paired level heads 0..3, tiles of up to ~200 KiB of rows and two bin
+ * buffers (few rows fit in shared memory, so bins hold many trees); else the
+ * values below.
  *   bin_size          B, trees per bin (Section III-A "stripe width"), 1..1024
- *                     (default 3)
+ *                     (default 3; wide rows 32)
  *   interleave_depth  d: each tree contributes 2^(d+1)-1 nodes (levels 0..d of
  *                     a complete tree) to its bin's interleaved block
  *                     (Section III-A), 0..9 for ranked heads, 0..11 for
- *                     level heads (default 9)
+ *                     level heads (default 9; wide rows 3)
  *   obs_tile          observations per work item of the traversal kernel,
- *                     a multiple of 32, up to 2048
+ *                     a multiple of 32, up to 2048 (default: ~96 KiB of rows,
+ *                     wide rows ~200 KiB; shrunk at upload to fit shared
+ *                     memory)
  *   warps_per_cta     warps per CTA of the traversal kernel, 1..32
  *   pass_bytes        bins are swept in groups ("passes") whose records fit in
  *                     this many bytes, so a pass stays resident in L2 while
@@ -119,8 +125,8 @@ typedef struct fp_forest_desc {
  *                     paths of Section III-A), walked by explicit targets;
  *                     0 = default: 2 when d is odd, else 1
  *   bin_buffers       shared-memory buffers that bin blocks stream through,
- *                     2 or 3 (0 = 3): two leave room for larger heads or
- *                     tiles, three hide copy latency better
+ *                     2 or 3 (0 = 3; wide rows 2): two leave room for larger
+ *                     heads or tiles, three hide copy latency better
  *   deep_levels       tree levels per 32-byte super-node below the head: 2
  *                     (full thresholds), 3 (thresholds as order keys, some
  *                     shortened to key prefixes, ties decided by a side

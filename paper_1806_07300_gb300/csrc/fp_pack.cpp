@@ -552,8 +552,15 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
     }
     fp_pack_params p = params ? *params : fp_pack_params{0, -1, 0, 0, 0, 0, 0, 0, 0, 0};
     const int32_t refill = p.refill_lanes ? p.refill_lanes : 32;
-    int32_t B = p.bin_size ? p.bin_size : 3;
-    const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : 9;
+    // Defaults.  Rows of at most 384 features: bins of 3 trees with paired
+    // level heads 0..9 and tiles of ~96 KiB of rows.  Wider rows (the
+    // 784-feature image workload) leave shared memory for few rows, so a bin
+    // should hold many trees (more tasks per bin block) with a small head:
+    // bins of 32 trees, paired heads 0..3, two bin buffers and tiles of up to
+    // ~200 KiB of rows, the launch measured best for such forests.
+    const bool wide_rows = F > 384;
+    int32_t B = p.bin_size ? p.bin_size : (wide_rows ? 32 : 3);
+    const int32_t d = p.interleave_depth >= 0 ? p.interleave_depth : (wide_rows ? 3 : 9);
     // head kind: 0 = default (paired level slots when d is odd, else level slots)
     const int32_t kind = p.head_select ? p.head_select : (d % 2 ? 2 : 1);
     const int32_t W = p.warps_per_cta ? p.warps_per_cta : 32;
@@ -574,8 +581,8 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
                                    : (auto1 ? 1 : (auto2 ? 2 : 0));
     const bool three = fmt != 0;
     int32_t R = p.obs_tile;
-    if (R == 0) {  // rows take up to ~96 KiB of shared memory
-        int64_t r = (96 * 1024) / ((int64_t)F * 4);
+    if (R == 0) {  // rows take up to ~96 KiB of shared memory (wide rows: ~200 KiB)
+        int64_t r = ((wide_rows ? 200 : 96) * 1024) / ((int64_t)F * 4);
         r = r / 32 * 32;
         R = (int32_t)std::max<int64_t>(32, std::min<int64_t>(1024, r));
     }
@@ -658,7 +665,7 @@ extern "C" int fp_pack_forest(const fp_forest_desc *desc, const fp_pack_params *
         h.head_select = kind;
         h.obs_tile = R; h.warps_per_cta = W;
         h.refill_lanes = refill;
-        h.bin_buffers = p.bin_buffers ? p.bin_buffers : 3;
+        h.bin_buffers = p.bin_buffers ? p.bin_buffers : (wide_rows ? 2 : 3);
         std::vector<FpBin> bins((size_t)n_bins);
         int64_t head_total = 0, phead_total = 0;
         int32_t max_head = 0;
