@@ -147,10 +147,16 @@ void (*batched_kernel(int kind, int hk))(BatchParams) {
     return batched_kernels()[(size_t)(4 * ki + (hk + 1))];
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel instance,
+// which every resident forest of the same kind of super-node, head kind and
+// CTA size shares: it is raised to the device's whole budget (a limit, not a
+// reservation; each launch asks for its own forest's bytes), so configuring
+// one forest never lowers it below another's need.  The grid comes from the
+// occupancy at this forest's own bytes.
 template <int MODE>
-int configure(fp_device_forest *f, size_t smem, int32_t *grid) {
+int configure(fp_device_forest *f, size_t smem, size_t budget, int32_t *grid) {
     auto kern = traverse_kernel<MODE>(f);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, f->threads, smem);
@@ -193,13 +199,13 @@ int launch_setup(fp_device_forest *f, int32_t tile, int32_t warps, int32_t refil
     g.nbuf = nbuf;
     g.smem_votes = smem_bytes(R, F, f->head_smem, nbuf, C, warps, false);
     g.smem_leaves = smem_bytes(R, F, f->head_smem, nbuf, C, warps, true);
-    int rc = configure<FP_MODE_VOTES>(&g, g.smem_votes, &g.grid_votes);
+    int rc = configure<FP_MODE_VOTES>(&g, g.smem_votes, budget, &g.grid_votes);
     if (rc) return rc;
-    rc = configure<FP_MODE_LEAVES>(&g, g.smem_leaves, &g.grid_leaves);
+    rc = configure<FP_MODE_LEAVES>(&g, g.smem_leaves, budget, &g.grid_leaves);
     if (rc) return rc;
     if (f->hdr.n_values > 0) {  // one float per row instead of the class votes
         g.smem_values = smem_bytes(R, F, f->head_smem, nbuf, 1, warps, false);
-        rc = configure<FP_MODE_VALUES>(&g, g.smem_values, &g.grid_values);
+        rc = configure<FP_MODE_VALUES>(&g, g.smem_values, budget, &g.grid_values);
         if (rc) return rc;
     }
     // the batched kernels may host any resident forest: allow them all of shared memory

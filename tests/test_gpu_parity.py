@@ -127,6 +127,38 @@ def test_tiny_multi_pass(tiny_forest, tiny_rows, pass_bytes, sel):
     _check_all(tiny_forest, X, bin_size=2, interleave_depth=1, pass_bytes=pass_bytes, obs_tile=128, head_select=sel)
 
 
+def test_resident_forests_sharing_a_kernel(tiny_forest, tiny_rows):
+    """Forests that run the same compiled kernel (same super-node kind, head
+    kind and CTA size) but need different shared memory (1024-row and 64-row
+    tiles) all stay usable, in every mode, whichever was uploaded or
+    configured last."""
+    X, _ = tiny_rows
+    ref = oracle.predict(tiny_forest, X)
+    Xd = _dev(X)
+    big = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=4, interleave_depth=3, obs_tile=1024))
+    small = fp.fp_upload(fp.fp_pack_forest(tiny_forest, bin_size=4, interleave_depth=3, obs_tile=64))
+    assert big.info["obs_tile"] > small.info["obs_tile"]
+
+    def check(df):
+        votes, cls = df.predict(Xd)
+        leaves = df.predict_leaves(Xd)
+        torch.cuda.synchronize()
+        assert df.sync_status() == fp.FP_OK
+        np.testing.assert_array_equal(votes.cpu().numpy().astype(np.uint32), ref["votes"])
+        np.testing.assert_array_equal(cls.cpu().numpy(), ref["cls"])
+        np.testing.assert_array_equal(leaves.cpu().numpy(), ref["leaf"])
+
+    for df in (big, small, big):
+        check(df)
+    small.configure(obs_tile=32)
+    check(big)
+    big.configure(obs_tile=512)
+    check(small)
+    check(big)
+    big.release()
+    small.release()
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33])
 def test_small_and_empty_batches(tiny_forest, tiny_rows, n):
     X, _ = tiny_rows
